@@ -1,0 +1,207 @@
+/*
+ * rrs.h - C ABI of the GB300 library for Refined Random Search (RRS)
+ * projection depths (arXiv 2506.08262, "Massive parallelization of
+ * projection-based depths").
+ *
+ * The library computes, for every query point z of a batch and a resident
+ * data cloud X (n x d), the RRS approximation of a depth that satisfies the
+ * projection property (Def. 2): the minimum over r rounds of m = ceil(k/r)
+ * directions u of the univariate depth D(u'z | u'X) (Sec. 2), where round 1
+ * draws directions uniformly on the sphere and round l >= 2 draws them in a
+ * spherical cap of angle (pi/2) alpha^(l-1) around the best direction found
+ * so far (Alg. 1, Alg. 4, Alg. S3, Alg. S4).
+ *
+ * All compute runs on one CUDA device in hand-written sm_103a kernels; there
+ * is no CPU fallback.  Pointers are plain host or device addresses as each
+ * argument states; no framework types cross this boundary.  Every function
+ * returns an rrs_status (0 = success, negative = error) and never throws.
+ * rrs_status_string() turns a status into text and rrs_last_error() gives
+ * the detail of the last failure on the calling thread.
+ *
+ * Thread safety: a context may be used from one host thread at a time.
+ */
+#ifndef RRS_H
+#define RRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rrs_ctx rrs_ctx;
+typedef int32_t rrs_status;
+
+/* Status codes. */
+#define RRS_OK 0
+#define RRS_ERR_INVALID_ARG (-1) /* bad size, kind, k < r, alpha outside (0,1], non-finite data */
+#define RRS_ERR_NOT_FOUND (-2)   /* unknown dataset id */
+#define RRS_ERR_BUDGET (-3)      /* the context's device-memory budget would be exceeded */
+#define RRS_ERR_CUDA (-4)        /* a CUDA runtime call failed (see rrs_last_error) */
+#define RRS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define RRS_ERR_INTERNAL (-6)    /* an internal invariant failed */
+#define RRS_ERR_UNSUPPORTED (-7) /* valid request this build cannot serve (e.g. d too large) */
+
+/* Element types of X and Z. */
+#define RRS_F32 0
+#define RRS_F64 1
+
+/* Depth notions (Sec. 2). */
+#define RRS_HALFSPACE 0        /* D_H = min(#{y <= y_z}, #{y >= y_z}) / n, closed halfspaces */
+#define RRS_PROJECTION 1       /* D_P = 1 / (1 + |y_z - med| / MAD), MAD unscaled */
+#define RRS_ASYM_PROJECTION 2  /* D_AP = 1 / (1 + (y_z - med)_+ / MAD_+) */
+
+/* Projection arithmetic. */
+#define RRS_PREC_FP32_SIMT 0     /* FP32 dot products on the CUDA cores */
+#define RRS_PREC_SPLIT_BF16X3 1  /* halfspace only: tcgen05 tensor cores, x*u as
+                                    x_hi u_hi + x_hi u_lo + x_lo u_hi (BF16 parts),
+                                    FP32 accumulation */
+
+/*
+ * rrs_create - open a context on CUDA device `device`.
+ *   hbm_budget_bytes: upper bound on the device memory the context may hold
+ *   for datasets and per-call workspace; 0 means no bound.
+ *   *out receives the context.  Errors: INVALID_ARG (out NULL, bad device),
+ *   CUDA.
+ */
+rrs_status rrs_create(rrs_ctx** out, int32_t device, uint64_t hbm_budget_bytes);
+
+/* rrs_destroy - free every dataset and workspace of the context, then the
+ * context.  NULL is accepted.  Work already queued by the context is
+ * synchronised first. */
+rrs_status rrs_destroy(rrs_ctx* ctx);
+
+/*
+ * rrs_register_dataset - copy a data cloud X into device memory and keep it
+ * resident (the paper's X, Sec. 2).
+ *   X: n x d row-major array of `dtype` (RRS_F32 or RRS_F64), on the device
+ *      if x_on_device != 0, else on the host.  The caller keeps ownership;
+ *      the library copies it and never reads X after returning.
+ *   n >= 1, 1 <= d <= 1024.  Every entry must be finite and of magnitude
+ *   below 2^64 (checked: INVALID_ARG).
+ *   *dataset_id_out receives a positive id valid until rrs_free/rrs_destroy.
+ * Errors: INVALID_ARG, BUDGET, CUDA.  Synchronous.
+ */
+rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t d, int32_t dtype,
+                                int32_t x_on_device, int64_t* dataset_id_out);
+
+/* rrs_free - release a registered dataset.  Errors: NOT_FOUND. */
+rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id);
+
+/*
+ * rrs_depth - RRS depth of every query of a batch (Alg. 4 run for each row of
+ * Z; rows are independent).
+ *   Z: n_queries x d row-major array of `dtype` (same d as the dataset), on
+ *      the device if z_on_device != 0.  n_queries may be 0 (no work).
+ *   kind: RRS_HALFSPACE, RRS_PROJECTION or RRS_ASYM_PROJECTION.
+ *   n_dirs (k) >= n_refinements (r) >= 1; m = ceil(k/r) directions per round.
+ *   cap_shrink (alpha) in (0, 1]; it is rounded to FP32 before use.
+ *   seed keys the Philox4x32-10 direction stream; query row q of this call
+ *   uses counter (block, j, l-1, q), so each result depends only on
+ *   (X, z, q, kind, k, r, alpha, seed) and not on what else is batched.
+ *   precision: RRS_PREC_FP32_SIMT, or RRS_PREC_SPLIT_BF16X3 for halfspace
+ *   depth.  Halfspace counts are exact either way: every point whose fast
+ *   projection lies in the near-tie band |u'x - u'z| <= b is re-checked
+ *   with an exact FP64 sign test.
+ * Outputs (each n_queries long, or n_queries*r for round_choice_out):
+ *   depth_out[q]   final depth D_min (double).                      required
+ *   count_out[q]   halfspace: min(#<=, #>=) at D_min, else -1.        optional
+ *   best_out[q]    flat index (l-1)*m + j of the direction that gave
+ *                  D_min, or -1 if no direction went below 1.         optional
+ *   round_choice_out[q*r + l-1]  index j taken as new pole in round l,
+ *                  or -1 if the pole was kept.                        optional
+ *   Outputs are device pointers if out_on_device != 0, else host pointers.
+ * stream: a cudaStream_t (NULL = the legacy default stream).  With host
+ *   outputs the call returns after the results are copied back.  With
+ *   device outputs it returns after enqueueing; inputs and outputs must then
+ *   stay valid until the stream has run.
+ * Errors: INVALID_ARG, NOT_FOUND, BUDGET, UNSUPPORTED, CUDA.
+ */
+rrs_status rrs_depth(rrs_ctx* ctx, int64_t dataset_id, const void* Z, int64_t n_queries,
+                     int32_t dtype, int32_t z_on_device, int32_t kind, int32_t n_dirs,
+                     int32_t n_refinements, double cap_shrink, uint64_t seed, int32_t precision,
+                     double* depth_out, int64_t* count_out, int32_t* best_out,
+                     int32_t* round_choice_out, int32_t out_on_device, void* stream);
+
+/*
+ * One request of a batched launch: a dataset, its query batch (device
+ * memory, row-major n_queries x d, FP32 or FP64 as `dtype`) and RRS
+ * parameters, with device output pointers as in rrs_depth.
+ */
+typedef struct rrs_request {
+    int64_t dataset_id;
+    const void* Z;
+    int64_t n_queries;
+    int32_t dtype;
+    int32_t kind;
+    int32_t n_dirs;
+    int32_t n_refinements;
+    double cap_shrink;
+    uint64_t seed;
+    double* depth_out;
+    int64_t* count_out;        /* optional */
+    int32_t* best_out;         /* optional */
+    int32_t* round_choice_out; /* optional */
+} rrs_request;
+
+/*
+ * rrs_depth_batched - run many independent requests (different datasets of
+ * uneven n and d, different kinds) together: every refinement round of every
+ * request is served by one launch per pipeline stage over all requests
+ * (Sec. 4: directions are independent within a round, queries are
+ * independent).  Results are identical to calling rrs_depth on each request
+ * alone with RRS_PREC_FP32_SIMT.  Requests may have different r; a request
+ * leaves the batch when its rounds are done.
+ *   reqs: host array of n_requests descriptors; all pointers inside are
+ *   device pointers.  use_graph != 0 captures the launch sequence into a
+ *   CUDA graph that is replayed on later calls with identical descriptors.
+ * Errors: as rrs_depth.  Stream-ordered on `stream`.
+ */
+rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_requests,
+                             int32_t use_graph, void* stream);
+
+/* Text for a status code (static storage). */
+const char* rrs_status_string(rrs_status status);
+
+/* Detail of the last failure on the calling thread (static, thread-local). */
+const char* rrs_last_error(void);
+
+/*
+ * rrs_debug_directions - write the m directions of round `round` (1-based)
+ * for query counter q into U (m x d FP32, row-major, device pointer), drawn
+ * around `pole` (d FP32, device pointer; ignored for round 1) with the
+ * library's generator.  Lets tests compare the device direction stream bit
+ * for bit with an independent implementation.  Synchronous.
+ */
+rrs_status rrs_debug_directions(rrs_ctx* ctx, uint64_t seed, int32_t q, int32_t round, int32_t m,
+                                int32_t d, double cap_shrink, const float* pole, float* U);
+
+/*
+ * rrs_debug_round_depths - for one dataset, query batch (device, FP32/FP64)
+ * and round, the univariate depth of every (query, direction) pair,
+ * with the directions supplied by the caller: U (n_queries x m x d FP32,
+ * device).  depth_out (n_queries x m, device) receives D(u'z | u'X);
+ * count_out (n_queries x m, device, halfspace only, may be NULL) receives
+ * min(#<=, #>=); band_out (n_queries x m, device, halfspace only, may be
+ * NULL) receives how many points fell in the near-tie band.  Synchronous.
+ */
+rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* Z,
+                                  int64_t n_queries, int32_t dtype, int32_t kind, int32_t m,
+                                  const float* U, int32_t precision, double* depth_out,
+                                  int64_t* count_out, int64_t* band_out);
+
+/* rrs_check - wait for `stream` (a cudaStream_t, NULL = legacy default) and
+ * report device-side failures flagged by earlier stream-ordered calls
+ * (INTERNAL), clearing the flags.  Use it after rrs_depth with device outputs
+ * or rrs_depth_batched. */
+rrs_status rrs_check(rrs_ctx* ctx, void* stream);
+
+/* Number of kernel launches this context has issued (for accounting). */
+uint64_t rrs_launch_count(rrs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RRS_H */

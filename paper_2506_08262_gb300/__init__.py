@@ -1,0 +1,273 @@
+"""Python binding of the GB300 RRS depth library (``include/rrs.h``).
+
+Every function named ``rrs_*`` here forwards to the C ABI function of the
+same name through ctypes: it only marshals arguments (torch tensors or numpy
+arrays to pointers, CUDA streams to handles) and raises ``RRSError`` on a
+non-zero status.  All computation runs in the sm_103a kernels of
+``_build/librrs.so``; if that library is missing or fails to load, importing
+the binding succeeds but every call raises, so nothing can silently fall back
+to another implementation.
+
+``Context`` is a small convenience wrapper that owns an ``rrs_ctx`` and takes
+torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librrs.so")
+
+RRS_OK = 0
+RRS_ERR_INVALID_ARG = -1
+RRS_ERR_NOT_FOUND = -2
+RRS_ERR_BUDGET = -3
+RRS_ERR_CUDA = -4
+RRS_ERR_TIMEOUT = -5
+RRS_ERR_INTERNAL = -6
+RRS_ERR_UNSUPPORTED = -7
+
+RRS_F32, RRS_F64 = 0, 1
+RRS_HALFSPACE, RRS_PROJECTION, RRS_ASYM_PROJECTION = 0, 1, 2
+RRS_PREC_FP32_SIMT, RRS_PREC_SPLIT_BF16X3 = 0, 1
+
+
+class RRSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status}")
+        self.status = status
+
+
+class rrs_request(ctypes.Structure):
+    _fields_ = [
+        ("dataset_id", ctypes.c_int64),
+        ("Z", ctypes.c_void_p),
+        ("n_queries", ctypes.c_int64),
+        ("dtype", ctypes.c_int32),
+        ("kind", ctypes.c_int32),
+        ("n_dirs", ctypes.c_int32),
+        ("n_refinements", ctypes.c_int32),
+        ("cap_shrink", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("depth_out", ctypes.c_void_p),
+        ("count_out", ctypes.c_void_p),
+        ("best_out", ctypes.c_void_p),
+        ("round_choice_out", ctypes.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "rrs_create": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64], ctypes.c_int32),
+    "rrs_destroy": ([ctypes.c_void_p], ctypes.c_int32),
+    "rrs_register_dataset": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_free": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
+    "rrs_depth": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                   ctypes.c_void_p], ctypes.c_int32),
+    "rrs_depth_batched": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p],
+                          ctypes.c_int32),
+    "rrs_status_string": ([ctypes.c_int32], ctypes.c_char_p),
+    "rrs_last_error": ([], ctypes.c_char_p),
+    "rrs_debug_directions": ([ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_debug_round_depths": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
+}
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects in librrs.so."""
+    return sorted(_SIGS)
+
+
+def load(path: Optional[str] = None):
+    """Load librrs.so (idempotent).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"librrs.so not built ({p}); run __graft_entry__.build() or "
+                               "python paper_2506_08262_gb300/build.py")
+        lib = ctypes.CDLL(p)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != RRS_OK:
+        lib = load()
+        detail = lib.rrs_last_error().decode(errors="replace")
+        name = lib.rrs_status_string(status).decode()
+        raise RRSError(status, f"{what} failed ({name}): {detail}")
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---- C ABI, same names ---------------------------------------------------------
+
+def rrs_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().rrs_create(ctypes.byref(h), device, hbm_budget_bytes), "rrs_create")
+    return h.value
+
+
+def rrs_destroy(ctx: int) -> None:
+    _check(load().rrs_destroy(ctx), "rrs_destroy")
+
+
+def rrs_register_dataset(ctx: int, X, n: int, d: int, dtype: int, x_on_device: bool) -> int:
+    out = ctypes.c_int64()
+    _check(load().rrs_register_dataset(ctx, _ptr(X), n, d, dtype, int(x_on_device), ctypes.byref(out)),
+           "rrs_register_dataset")
+    return out.value
+
+
+def rrs_free(ctx: int, dataset_id: int) -> None:
+    _check(load().rrs_free(ctx, dataset_id), "rrs_free")
+
+
+def rrs_depth(ctx: int, dataset_id: int, Z, n_queries: int, dtype: int, z_on_device: bool, kind: int, n_dirs: int,
+              n_refinements: int, cap_shrink: float, seed: int, precision: int, depth_out, count_out=None,
+              best_out=None, round_choice_out=None, out_on_device: bool = True, stream=None) -> None:
+    _check(load().rrs_depth(ctx, dataset_id, _ptr(Z), n_queries, dtype, int(z_on_device), kind, n_dirs,
+                            n_refinements, float(cap_shrink), seed, precision, _ptr(depth_out), _ptr(count_out),
+                            _ptr(best_out), _ptr(round_choice_out), int(out_on_device), _stream(stream)),
+           "rrs_depth")
+
+
+def rrs_depth_batched(ctx: int, reqs, use_graph: bool = False, stream=None) -> None:
+    arr = (rrs_request * len(reqs))(*reqs)
+    _check(load().rrs_depth_batched(ctx, arr, len(reqs), int(use_graph), _stream(stream)), "rrs_depth_batched")
+
+
+def rrs_debug_directions(ctx: int, seed: int, q: int, round: int, m: int, d: int, cap_shrink: float, pole,
+                         U) -> None:
+    _check(load().rrs_debug_directions(ctx, seed, q, round, m, d, float(cap_shrink), _ptr(pole), _ptr(U)),
+           "rrs_debug_directions")
+
+
+def rrs_debug_round_depths(ctx: int, dataset_id: int, Z, n_queries: int, dtype: int, kind: int, m: int, U,
+                           precision: int, depth_out, count_out=None, band_out=None) -> None:
+    _check(load().rrs_debug_round_depths(ctx, dataset_id, _ptr(Z), n_queries, dtype, kind, m, _ptr(U), precision,
+                                         _ptr(depth_out), _ptr(count_out), _ptr(band_out)),
+           "rrs_debug_round_depths")
+
+
+def rrs_check(ctx: int, stream=None) -> None:
+    _check(load().rrs_check(ctx, _stream(stream)), "rrs_check")
+
+
+def rrs_launch_count(ctx: int) -> int:
+    return int(load().rrs_launch_count(ctx))
+
+
+def rrs_status_string(status: int) -> str:
+    return load().rrs_status_string(status).decode()
+
+
+def rrs_last_error() -> str:
+    return load().rrs_last_error().decode(errors="replace")
+
+
+# ---- convenience wrapper over torch tensors -------------------------------------
+
+class Context:
+    """Owns an ``rrs_ctx``; datasets and queries are torch tensors (CPU or CUDA)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.handle = rrs_create(device, hbm_budget_bytes)
+        self._dims = {}
+
+    def close(self):
+        if self.handle:
+            rrs_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _dtype_code(t) -> int:
+        import torch
+        if t.dtype == torch.float32:
+            return RRS_F32
+        if t.dtype == torch.float64:
+            return RRS_F64
+        raise TypeError("X and Z must be float32 or float64")
+
+    def register(self, X) -> int:
+        X = X.contiguous()
+        n, d = X.shape
+        did = rrs_register_dataset(self.handle, X, n, d, self._dtype_code(X), X.is_cuda)
+        self._dims[did] = d
+        return did
+
+    def free(self, dataset_id: int):
+        rrs_free(self.handle, dataset_id)
+        self._dims.pop(dataset_id, None)
+
+    def depth(self, dataset_id: int, Z, kind: int, k: int, r: int, alpha: float, seed: int = 0,
+              precision: int = RRS_PREC_FP32_SIMT, stream=None, rounds: bool = False):
+        """RRS depth of every row of Z; returns CUDA tensors (depth, count, best[, choice])."""
+        import torch
+        Z = Z.contiguous()
+        nq = Z.shape[0]
+        dev = torch.device("cuda", self.device)
+        depth = torch.empty(nq, dtype=torch.float64, device=dev)
+        count = torch.empty(nq, dtype=torch.int64, device=dev)
+        best = torch.empty(nq, dtype=torch.int32, device=dev)
+        choice = torch.empty((nq, r), dtype=torch.int32, device=dev) if rounds else None
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        rrs_depth(self.handle, dataset_id, Z, nq, self._dtype_code(Z), Z.is_cuda, kind, k, r, alpha, seed,
+                  precision, depth, count, best, choice, True, stream)
+        rrs_check(self.handle, stream)
+        return (depth, count, best, choice) if rounds else (depth, count, best)

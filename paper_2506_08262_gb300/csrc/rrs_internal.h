@@ -1,0 +1,110 @@
+// Internal structures shared by the host runtime (rrs_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rrs {
+
+// A resident dataset, as the kernels see it.
+struct DsDev {
+    const float* X32;      // n x ldx FP32 rows, zero padded
+    const double* X64;     // n x d FP64 rows, or nullptr if the data came in FP32
+    const float* xnorm;    // n Euclidean row norms, rounded up
+    const uint16_t* Xbf;   // n x (2*kp) BF16 planes [x_hi | x_lo] for the tensor-core path, or nullptr
+    int64_t n;
+    int32_t d;
+    int32_t ldx;           // padded FP32 row stride (floats)
+    int32_t kp;            // padded K of one BF16 plane (multiple of 64), 0 if no planes
+    int32_t pad;
+};
+
+// One query of a launch (any request, any dataset).
+struct SlotDev {
+    int32_t ds;            // index into the DsDev array
+    int32_t kind;
+    int32_t m;             // directions per round
+    int32_t r;             // rounds
+    float alpha;
+    int32_t d;
+    int32_t ldx;
+    int32_t zdtype;        // 0 = FP32, 1 = FP64
+    uint64_t seed;
+    int64_t qctr;          // query counter index in the direction stream
+    int64_t uoff;          // offset of this slot's m x ldx directions in U (floats)
+    int64_t roff;          // offset of this slot's m results / y_z values
+    int64_t zoff32;        // offset of the FP32 query row (ldx floats) and of the poles
+    int64_t zoff64;        // offset of the FP64 query row (d doubles)
+    const void* zsrc;      // caller's query row (device)
+    double* depth_out;     // this query's output cells (device), may be null
+    int64_t* count_out;
+    int32_t* best_out;
+    int32_t* choice_out;   // r cells
+    // running state (Alg. 1 step 5)
+    double dmin;
+    int64_t cmin;
+    int32_t best;
+    float znorm;
+};
+
+// A block of directions of one slot handled by one CTA.
+struct TaskDev {
+    int32_t slot;
+    int32_t j0;
+    int32_t nj;
+    int32_t pad;
+};
+
+// Per (slot, direction) result of one round.
+struct ResDev {
+    double depth;
+    int64_t count;         // halfspace: min(#<=, #>=); else -1
+};
+
+// Device-side error bits (ORed into one word).
+enum : int {
+    ERR_SELECT_ITER = 1,    // bucket selection did not converge
+    ERR_SELECT_CAP = 2,
+    ERR_EXPANSION = 4,      // exact-sign expansion overflow
+    ERR_TIMEOUT = 8,
+    ERR_TC_SETUP = 16,
+};
+
+// Near-tie band factors: a point is re-checked exactly when
+// |t| <= gamma * (|x| + |z|), t the fast projection difference.
+__host__ __device__ float band_gamma_fp32(int d);
+float band_gamma_tc(int d);
+
+// launchers (rrs_kernels.cu)
+cudaError_t launch_prep(const SlotDev* slots, int nslots, const DsDev* ds, float* z32, double* z64,
+                        float* poles, cudaStream_t st);
+cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles_cur,
+                       const double* z64, float* U, double* yz, int round0, cudaStream_t st);
+cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const SlotDev* slots, const DsDev* ds,
+                           const float* U, const double* yz, const double* z64, ResDev* res, int64_t* band_out,
+                           int* err, cudaStream_t st);
+cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
+                        const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st);
+cudaError_t launch_argmin(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
+                          const ResDev* res, const float* poles_cur, float* poles_next, int round0,
+                          int last_round, cudaStream_t st);
+cudaError_t launch_yz_only(const TaskDev* tasks, int ntasks, const SlotDev* slots, const double* z64,
+                           const float* U, double* yz, cudaStream_t st);
+cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, float alpha, const float* pole,
+                              float* U, cudaStream_t st);
+cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, int ldx, float* X32,
+                                   double* X64, float* xnorm, int* bad, cudaStream_t st);
+cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
+size_t pdap_smem_bytes(int n, int group, int ldx);
+int pdap_max_group(int n, int ldx, int m);
+
+// tensor-core path (hd_tc.cu)
+cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
+                                     cudaStream_t st);
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds,
+                         const float* U, const double* yz, const double* z64, ResDev* res,
+                         int64_t* band_out, int* err, cudaStream_t st);
+bool hd_tc_supported(int d);
+
+}  // namespace rrs

@@ -1,0 +1,40 @@
+"""CPU checks of the boundary: the library builds, loads, exports every entry
+point that include/rrs.h declares, and reports errors without a GPU."""
+import os
+import re
+
+import pytest
+
+import paper_2506_08262_gb300 as rrs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "rrs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:rrs_status|const char\*|uint64_t)\s+(rrs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2506_08262_gb300 import build
+    build.build()
+    lib = rrs.load()
+    decl = declared_functions()
+    assert len(decl) >= 10
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(decl) == set(rrs.exported_symbols())
+
+
+def test_status_strings_and_no_gpu_error():
+    assert rrs.rrs_status_string(rrs.RRS_ERR_BUDGET) == "device memory budget exceeded"
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(rrs.RRSError) as e:
+        rrs.rrs_create(0)
+    assert e.value.status in (rrs.RRS_ERR_CUDA, rrs.RRS_ERR_INVALID_ARG)
