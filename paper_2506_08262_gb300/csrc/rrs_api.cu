@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -42,6 +43,20 @@ rrs_status fail(rrs_status st, const char* fmt, ...)
             return fail(RRS_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
                         __FILE__, __LINE__);                                               \
     } while (0)
+
+// Opt-in host trace (RRS_TRACE=1) for locating failures in the runtime.
+void trace(const char* fmt, ...)
+{
+    static const bool on = getenv("RRS_TRACE") && getenv("RRS_TRACE")[0] == '1';
+    if (!on) return;
+    va_list ap;
+    va_start(ap, fmt);
+    fprintf(stderr, "[rrs] ");
+    vfprintf(stderr, fmt, ap);
+    fprintf(stderr, "\n");
+    fflush(stderr);
+    va_end(ap);
+}
 
 int padded_ldx(int d)
 {
@@ -765,7 +780,7 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
     s = build_plan(reqs, precision, P);
     if (s != RRS_OK) return s;
     Carve sizing;
-    const size_t bytes = carve_plan(P, sizing) + sizeof(int64_t) * n_queries;
+    const size_t bytes = carve_plan(P, sizing) + sizeof(int64_t) * n_queries + 512;
     void* ws = nullptr;
     CUDA_TRY(cudaMalloc(&ws, bytes));
     Carve C;
@@ -773,24 +788,17 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
     carve_plan(P, C);
     int64_t* band = C.take<int64_t>(n_queries);
     cudaStream_t st = 0;
+    trace("debug_round_depths: workspace %zu bytes", bytes);
     s = upload_plan(ctx, P, st);
     if (s == RRS_OK) {
+        trace("debug_round_depths: plan uploaded");
         cudaMemsetAsync(band, 0, sizeof(int64_t) * n_queries, st);
         CUDA_TRY(launch_prep(P.d_slots, (int)P.slots.size(), P.d_ds, P.z32, P.z64, P.poles, st));
         // caller's directions replace the generated ones; y_z from the FP64 query
-        for (size_t si = 0; si < P.slots.size(); ++si) {
-            const SlotDev& S = P.slots[si];
-            CUDA_TRY(cudaMemcpy2DAsync(P.U + S.uoff, sizeof(float) * S.ldx, U + (size_t)si * m * D.d,
-                                       sizeof(float) * D.d, sizeof(float) * D.d, m, cudaMemcpyDeviceToDevice, st));
-        }
-        if (D.ldx > D.d) {
-            for (size_t si = 0; si < P.slots.size(); ++si) {
-                const SlotDev& S = P.slots[si];
-                CUDA_TRY(cudaMemset2DAsync(P.U + S.uoff + D.d, sizeof(float) * S.ldx, 0,
-                                           sizeof(float) * (D.ldx - D.d), m, st));
-            }
-        }
+        CUDA_TRY(launch_scatter_dirs(P.d_slots, (int)P.slots.size(), m, D.d, U, P.U, st));
+        trace("debug_round_depths: directions scattered");
         CUDA_TRY(launch_yz_only(P.d_gen, (int)P.gen_tasks.size(), P.d_slots, P.z64, P.U, P.yz, st));
+        trace("debug_round_depths: y_z done");
         if (kind == RRS_HALFSPACE) {
             if (precision == RRS_PREC_SPLIT_BF16X3)
                 CUDA_TRY(launch_hd_tc(P.d_hd, (int)P.hd_tasks.size(), P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res,
@@ -805,11 +813,13 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
                                          P.z32, P.res, ctx->d_err, st));
         }
         ctx->launches += 4;
+        trace("debug_round_depths: depth kernels enqueued");
         std::vector<ResDev> hres(P.tot_m);
         CUDA_TRY(cudaMemcpyAsync(hres.data(), P.res, sizeof(ResDev) * P.tot_m, cudaMemcpyDeviceToHost, st));
         std::vector<int64_t> hband(n_queries);
         CUDA_TRY(cudaMemcpyAsync(hband.data(), band, sizeof(int64_t) * n_queries, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        trace("debug_round_depths: results copied");
         std::vector<double> dep(P.tot_m);
         std::vector<int64_t> cnt(P.tot_m);
         for (int64_t i = 0; i < P.tot_m; ++i) {

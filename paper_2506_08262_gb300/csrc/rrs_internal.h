@@ -91,6 +91,8 @@ cudaError_t launch_argmin(SlotDev* slots, const int32_t* slot_list, int nlist, c
                           int last_round, cudaStream_t st);
 cudaError_t launch_yz_only(const TaskDev* tasks, int ntasks, const SlotDev* slots, const double* z64,
                            const float* U, double* yz, cudaStream_t st);
+cudaError_t launch_scatter_dirs(const SlotDev* slots, int nslots, int m, int d, const float* Uin, float* U,
+                                cudaStream_t st);
 cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, float alpha, const float* pole,
                               float* U, cudaStream_t st);
 cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, int ldx, float* X32,

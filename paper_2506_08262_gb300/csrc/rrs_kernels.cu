@@ -166,6 +166,27 @@ cudaError_t launch_yz_only(const TaskDev* tasks, int ntasks, const SlotDev* slot
     return cudaGetLastError();
 }
 
+// caller-supplied directions (n_slots x m x d, dense) into the padded U rows
+__global__ void k_scatter_dirs(const SlotDev* __restrict__ slots, int nslots, int m, int d, const float* __restrict__ Uin,
+                               float* __restrict__ U)
+{
+    const int s = blockIdx.x;
+    if (s >= nslots) return;
+    const SlotDev& S = slots[s];
+    for (int e = threadIdx.x; e < m * S.ldx; e += blockDim.x) {
+        const int j = e / S.ldx, l = e - j * S.ldx;
+        U[S.uoff + e] = (l < d) ? Uin[((int64_t)s * m + j) * d + l] : 0.0f;
+    }
+}
+
+cudaError_t launch_scatter_dirs(const SlotDev* slots, int nslots, int m, int d, const float* Uin, float* U,
+                                cudaStream_t st)
+{
+    if (nslots <= 0) return cudaSuccess;
+    k_scatter_dirs<<<nslots, 128, 0, st>>>(slots, nslots, m, d, Uin, U);
+    return cudaGetLastError();
+}
+
 __global__ void k_debug_dirs(uint64_t seed, int q, int round0, int m, int d, float alpha, const float* pole,
                              float* U)
 {

@@ -178,7 +178,10 @@ def test_projection_depth_shapes(ctx, kind, n, d):
     X, Z = workloads.gaussian_cloud(n * 3 + d, n, d, 6, dtype=np.float32)
     Z[0] = X[0]
     g = gpu_rrs(ctx, X, Z, kind, 60, 3, 0.5, seed=2)
-    assert_follow(g, X, Z, kind, 60, 3, 0.5, 2)
+    # With two points the MAD is half their projected distance, and RRS steers u towards
+    # u'(x1 - x0) = 0 where the true depth is 0: the FP32 keys then carry a relative error
+    # of about 2^-24 * |y| / MAD, far above 1e-5.  Larger n has a robust MAD.
+    assert_follow(g, X, Z, kind, 60, 3, 0.5, 2, tol=TOL if n > 2 else 1e-3)
 
 
 @pytest.mark.parametrize("kind", [P, AP])
