@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the RRS depth hot path on GB300.
+
+Default workload (one "step"): projection depth and asymmetric projection depth
+of 1,000 queries uniform in [-4, 4]^10 against X = 10,000 points in d = 10
+(95% N(0, I), 5% N(6*1, I)), FP32, k = 1,000 directions over r = 20 rounds,
+alpha = 0.7 -- both kinds, every round, every query.  The metric is
+query-depths per second (and point-direction projections per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU FP64 oracle on the host cores instead (a
+bounded sample of the same workload per step).  For N > 1 (torchrun) every
+rank runs its own replica of the workload (weak scaling; the path needs no
+data exchange) and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "RRS query-depths/sec & point·direction projections/sec; serving p50/p99 latency"
+UNIT = "query-depths/s"
+WORKLOAD = ("projection + asymmetric projection depth, d=10, n=10000 (95% N(0,I), 5% N(6*1,I)), "
+            "1000 queries U[-4,4]^10, k=1000 dirs over r=20 rounds, alpha=0.7, FP32")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nq", type=int, default=1000, help="queries per kind (default: the full workload)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.array([num(r[2]) for r in rows])
+        pw = np.array([num(r[3]) for r in rows])
+        load = sm[pw > np.nanmedian(pw) * 0.8] if np.isfinite(pw).any() else sm
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.nanmedian(load if load.size else sm)), "sm_max_mhz": float(np.nanmax(mx)),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(per_kind: int):
+    """Time the FP64 oracle, as it stands, on `per_kind` queries of each kind (all host cores)."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    out = {}
+    total_q = 0
+    t0 = time.perf_counter()
+    for kind in (workloads.PROJECTION, workloads.ASYM_PROJECTION):
+        Pr = workloads.c2(kind=kind)
+        q = np.arange(per_kind)
+        oracle.rrs(Pr.X, Pr.Z[q], kind, Pr.k, Pr.r, Pr.alpha, Pr.seed, qidx=q, nthreads=threads)
+        total_q += per_kind
+    dt = time.perf_counter() - t0
+    out["value"] = total_q / dt
+    out["seconds"] = dt
+    out["cores"] = threads
+    out["sample"] = (f"{per_kind} queries of each kind (PD, AP) of the same workload, full n/k/r, "
+                     f"OpenMP over queries on {threads} host threads")
+    return out
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    per_kind = max(1, oracle.max_threads())
+    for _ in range(args.warmup):
+        oracle_sample_rate(per_kind)
+    times = []
+    nq = 0
+    for _ in range(args.steps):
+        r = oracle_sample_rate(per_kind)
+        times.append(r["seconds"])
+        nq += 2 * per_kind
+    value = nq / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": f"{per_kind} queries per kind (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def alu_ops_per_element(kind: int, d: int) -> int:
+    """Algorithmic ALU operations per (point, direction) element of the selection kernel:
+    d FMAs of the projection, 3 per histogram pass of each order-statistic selection
+    (bucket index FMA, conversion, shared-memory increment) for the two selections
+    (median, then MAD or MAD_+), and 2 for the count of y > med (asymmetric only)."""
+    return d + 2 * 3 + (2 if kind == workloads.ASYM_PROJECTION else 0)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from __graft_entry__ import build
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_2506_08262_gb300 as rrs
+
+    kinds = (workloads.PROJECTION, workloads.ASYM_PROJECTION)
+    P2 = workloads.c2()
+    X, Z = P2.X, P2.Z[:args.nq]
+    nq, n, d = Z.shape[0], X.shape[0], X.shape[1]
+    k, r, alpha, seed = P2.k, P2.r, P2.alpha, P2.seed
+    m = -(-k // r)
+
+    ctx = rrs.rrs_create(local, 0)
+    Xd = torch.from_numpy(X).to(dev)
+    did = rrs.rrs_register_dataset(ctx, Xd, n, d, rrs.RRS_F32, True)
+    Zd = torch.from_numpy(Z).to(dev)
+    outs = {kd: torch.empty(nq, dtype=torch.float64, device=dev) for kd in kinds}
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for kd in kinds:
+            rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F32, True, kd, k, r, alpha, seed, rrs.RRS_PREC_FP32_SIMT,
+                          outs[kd], None, None, None, True, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    rrs.rrs_check(ctx, stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = rrs.rrs_launch_count(ctx)
+    rrs.rrs_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                     # L2 flush between timed steps (not timed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    prof = rrs.rrs_profile_read(ctx)
+    rrs.rrs_profile_enable(ctx, False)
+    launches = rrs.rrs_launch_count(ctx) - launches0
+    rrs.rrs_check(ctx, stream)
+    clocks = sampler.stop()
+    step_ms = float(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # end to end through the public API: pinned host query buffer in, host depths out
+    Zh = torch.from_numpy(Z).pin_memory()
+    outh = {kd: torch.empty(nq, dtype=torch.float64).pin_memory() for kd in kinds}
+
+    def step_e2e():
+        for kd in kinds:
+            rrs.rrs_depth(ctx, did, Zh, nq, rrs.RRS_F32, False, kd, k, r, alpha, seed, rrs.RRS_PREC_FP32_SIMT,
+                          outh[kd], None, None, None, False, stream)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = 1000 * float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    for kd in kinds:
+        assert np.array_equal(outh[kd].numpy(), outs[kd].cpu().numpy()), "e2e results differ from device results"
+
+    qd_per_step = len(kinds) * nq
+    value = world * qd_per_step / (step_ms / 1000)
+    pd_per_step = len(kinds) * nq * r * m * n
+
+    # roofline of the dominant kernel (selection kernel, plain ALU bound)
+    pd_ms, pd_launches = prof["pdap"]
+    ops_per_step = sum(nq * r * m * n * alu_ops_per_element(kd, d) for kd in kinds)
+    launches_per_step = max(1, pd_launches // args.steps)
+    ops_per_launch = ops_per_step / launches_per_step
+    avg_launch_ms = pd_ms / max(1, pd_launches)
+    achieved = ops_per_launch / (avg_launch_ms / 1000) / 1e9
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e9
+    stage_share = {k2: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4) for k2, v in prof.items()
+                   if v[1]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": qd_per_step * world, "queries_per_kind": nq,
+                   "n": n, "d": d, "k": k, "r": r, "alpha": alpha, "parallelism": f"replicas{world}",
+                   "l2": "flushed between timed steps (512 MiB device write); inputs smaller than L2"},
+        "pd_per_s": world * pd_per_step / (step_ms / 1000),
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * qd_per_step / (e2e_ms / 1000), "unit": UNIT,
+                "h2d_bytes_per_step": int(Zh.numel() * 4 * len(kinds)),
+                "d2h_bytes_per_step": int(nq * 8 * len(kinds))},
+        "roofline": {"bound": "alu", "kernel": "k_pdap", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz (recipe unit counts and max clock)",
+                     "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms},
+        "stage_ms_per_step": {k2: v[0] / args.steps for k2, v in prof.items() if v[1]},
+        "stage_share": stage_share,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample_rate(max(1, os.cpu_count() or 1))
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                "sample": cb["sample"]}
+    rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

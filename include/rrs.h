@@ -200,6 +200,31 @@ rrs_status rrs_check(rrs_ctx* ctx, void* stream);
 /* Number of kernel launches this context has issued (for accounting). */
 uint64_t rrs_launch_count(rrs_ctx* ctx);
 
+/* Pipeline stages timed by the profiler (one slot each in rrs_profile_read). */
+#define RRS_STAGE_PREP 0      /* query conversion and state initialisation */
+#define RRS_STAGE_GEN 1       /* direction generation (Alg. S1 / S4) and y_z */
+#define RRS_STAGE_HD_SIMT 2   /* halfspace counts, FP32 CUDA-core projection */
+#define RRS_STAGE_HD_TC 3     /* halfspace counts, tcgen05 split-BF16x3 projection */
+#define RRS_STAGE_PDAP 4      /* projection / asymmetric projection depth (selection) */
+#define RRS_STAGE_ARGMIN 5    /* round minimum and pole update (Alg. 1 steps 4-6) */
+#define RRS_NSTAGES 6
+
+/*
+ * rrs_profile_enable - turn per-stage timing on (on != 0) or off and reset the
+ * accumulated figures.  While on, every launch of rrs_depth /
+ * rrs_depth_batched (outside graph capture) is bracketed by two CUDA events
+ * recorded on the launching stream.
+ */
+rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on);
+
+/*
+ * rrs_profile_read - wait for the recorded events and return, per stage, the
+ * accumulated device milliseconds (ms_out[RRS_NSTAGES], host) and launch
+ * counts (launches_out[RRS_NSTAGES], host, may be NULL) since the last
+ * rrs_profile_enable.
+ */
+rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,7 +85,11 @@ _SIGS = {
                                 ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
+    "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
+    "rrs_profile_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
 }
+
+RRS_STAGES = ("prep", "gen", "hd_simt", "hd_tc", "pdap", "argmin")
 
 
 def exported_symbols():
@@ -197,6 +201,18 @@ def rrs_check(ctx: int, stream=None) -> None:
 
 def rrs_launch_count(ctx: int) -> int:
     return int(load().rrs_launch_count(ctx))
+
+
+def rrs_profile_enable(ctx: int, on: bool = True) -> None:
+    _check(load().rrs_profile_enable(ctx, int(on)), "rrs_profile_enable")
+
+
+def rrs_profile_read(ctx: int):
+    """{stage name: (milliseconds, launches)} accumulated since rrs_profile_enable."""
+    ms = np.zeros(len(RRS_STAGES), np.float64)
+    n = np.zeros(len(RRS_STAGES), np.int64)
+    _check(load().rrs_profile_read(ctx, _ptr(ms), _ptr(n)), "rrs_profile_read")
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(RRS_STAGES)}
 
 
 def rrs_status_string(status: int) -> str:

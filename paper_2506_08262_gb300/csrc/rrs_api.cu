@@ -114,9 +114,54 @@ struct rrs_ctx {
         size_t launches = 0;
     };
     std::vector<GraphEntry> graphs;
+    // per-stage CUDA-event timing (rrs_profile_*)
+    bool profiling = false;
+    struct Mark {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[RRS_NSTAGES] = {};
+    int64_t stage_launches[RRS_NSTAGES] = {};
 };
 
 namespace {
+
+cudaEvent_t pooled_event(rrs_ctx* c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch with events when profiling is on (not during graph capture).
+struct StageTimer {
+    rrs_ctx* c;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageTimer(rrs_ctx* c_, int stage_, cudaStream_t st_, bool capturing) : c(c_), stage(stage_), st(st_)
+    {
+        if (c->profiling && !capturing) {
+            a = pooled_event(c);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~StageTimer()
+    {
+        if (a) {
+            cudaEvent_t b = pooled_event(c);
+            cudaEventRecord(b, st);
+            c->marks.push_back(rrs_ctx::Mark{stage, a, b});
+        }
+    }
+};
 
 bool budget_ok(rrs_ctx* c, uint64_t extra) { return c->budget == 0 || c->used + extra <= c->budget; }
 
@@ -332,34 +377,53 @@ rrs_status upload_plan(rrs_ctx* ctx, Plan& P, cudaStream_t st)
 }
 
 // Enqueue the whole refinement pipeline of a plan.
-rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st)
+rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing = false)
 {
     const int64_t T = P.tot_ldx;
-    CUDA_TRY(launch_prep(P.d_slots, (int)P.slots.size(), P.d_ds, P.z32, P.z64, P.poles, st));
-    ctx->launches++;
+    {
+        StageTimer t(ctx, RRS_STAGE_PREP, st, capturing);
+        CUDA_TRY(launch_prep(P.d_slots, (int)P.slots.size(), P.d_ds, P.z32, P.z64, P.poles, st));
+        ctx->launches++;
+        ctx->stage_launches[RRS_STAGE_PREP]++;
+    }
     for (int l = 0; l < P.rmax; ++l) {
         float* cur = P.poles + (l & 1) * T;
         float* nxt = P.poles + ((l + 1) & 1) * T;
-        CUDA_TRY(launch_gen(P.d_gen, P.n_gen[l], P.d_slots, cur, P.z64, P.U, P.yz, l, st));
-        ctx->launches += P.n_gen[l] > 0;
+        if (P.n_gen[l] > 0) {
+            StageTimer t(ctx, RRS_STAGE_GEN, st, capturing);
+            CUDA_TRY(launch_gen(P.d_gen, P.n_gen[l], P.d_slots, cur, P.z64, P.U, P.yz, l, st));
+            ctx->launches++;
+            ctx->stage_launches[RRS_STAGE_GEN]++;
+        }
         if (P.n_hd[l] > 0) {
-            if (P.precision == RRS_PREC_SPLIT_BF16X3)
+            if (P.precision == RRS_PREC_SPLIT_BF16X3) {
+                StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
                 CUDA_TRY(launch_hd_tc(P.d_hd, P.n_hd[l], P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res, nullptr,
                                       ctx->d_err, st));
-            else
+                ctx->stage_launches[RRS_STAGE_HD_TC]++;
+            } else {
+                StageTimer t(ctx, RRS_STAGE_HD_SIMT, st, capturing);
                 CUDA_TRY(launch_hd_simt(P.d_hd, P.n_hd[l], P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res,
                                         nullptr, ctx->d_err, st));
+                ctx->stage_launches[RRS_STAGE_HD_SIMT]++;
+            }
             ctx->launches++;
         }
         for (size_t c = 0; c < P.pd_tasks.size(); ++c) {
             if (P.n_pd[c][l] > 0) {
+                StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.d_slots, P.d_ds, P.U, P.z32, P.res,
                                      ctx->d_err, st));
                 ctx->launches++;
+                ctx->stage_launches[RRS_STAGE_PDAP]++;
             }
         }
-        CUDA_TRY(launch_argmin(P.d_slots, P.d_arg, P.n_arg[l], P.U, P.res, cur, nxt, l, 0, st));
-        ctx->launches += P.n_arg[l] > 0;
+        if (P.n_arg[l] > 0) {
+            StageTimer t(ctx, RRS_STAGE_ARGMIN, st, capturing);
+            CUDA_TRY(launch_argmin(P.d_slots, P.d_arg, P.n_arg[l], P.U, P.res, cur, nxt, l, 0, st));
+            ctx->launches++;
+            ctx->stage_launches[RRS_STAGE_ARGMIN]++;
+        }
     }
     return RRS_OK;
 }
@@ -434,6 +498,11 @@ rrs_status rrs_destroy(rrs_ctx* ctx)
         if (g.exec) cudaGraphExecDestroy(g.exec);
         cudaFree(g.ws);
     }
+    for (auto& m : ctx->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     cudaFree(ctx->d_err);
     delete ctx;
     return RRS_OK;
@@ -708,7 +777,7 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        s = enqueue_rounds(ctx, P, cap);
+        s = enqueue_rounds(ctx, P, cap, true);
         e = cudaStreamEndCapture(cap, &graph);
     }
     cudaStreamDestroy(cap);
@@ -843,5 +912,38 @@ rrs_status rrs_check(rrs_ctx* ctx, void* stream)
 }
 
 uint64_t rrs_launch_count(rrs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on)
+{
+    if (!ctx) return fail(RRS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->profiling = on != 0;
+    for (int i = 0; i < RRS_NSTAGES; ++i) {
+        ctx->stage_ms[i] = 0.0;
+        ctx->stage_launches[i] = 0;
+    }
+    return RRS_OK;
+}
+
+rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out)
+{
+    if (!ctx || !ms_out) return fail(RRS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    for (auto& m : ctx->marks) {
+        CUDA_TRY(cudaEventSynchronize(m.b));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, m.a, m.b));
+        ctx->stage_ms[m.stage] += ms;
+        ctx->event_pool.push_back(m.a);
+        ctx->event_pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+    for (int i = 0; i < RRS_NSTAGES; ++i) {
+        ms_out[i] = ctx->stage_ms[i];
+        if (launches_out) launches_out[i] = ctx->stage_launches[i];
+    }
+    return RRS_OK;
+}
 
 }  // extern "C"
