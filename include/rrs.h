@@ -225,6 +225,45 @@ rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on);
  */
 rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out);
 
+/*
+ * rrs_depth_noalloc - rrs_depth for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Callers such as plug-ins living inside another framework's memory pool,
+ * processes that forbid allocation once running, or loops that must never
+ * wait on the allocator cannot call cudaMalloc.  This call runs the same
+ * kernels as rrs_depth with RRS_PREC_FP32_SIMT, but takes the data cloud
+ * directly (no rrs_register_dataset, no context) and draws all its working
+ * memory from one fixed device array of RRS_NOALLOC_SCRATCH_BYTES that the
+ * library holds on every device that loads it, until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   X: n x d row-major, dtype RRS_F32 or RRS_F64, device pointer (read only;
+ *      for RRS_F64 the exact recheck reads it during the call).
+ *   Z: n_queries x d row-major, same dtype, device pointer.
+ *   kind, n_dirs, n_refinements, cap_shrink, seed: as rrs_depth; query row q
+ *      uses stream counter q, so results equal rrs_depth's bit for bit.
+ *   depth_out (n_queries doubles) and count_out (n_queries int64, halfspace
+ *      counts, or -1; may be NULL): device pointers.
+ *   stream: cudaStream_t (NULL = legacy default stream).  The call returns
+ *      after the stream has finished its work.
+ * Limits: everything the call needs (about 4*(n+1)*(d+4) bytes for X plus
+ * about n_queries * m * 4*(d+10) bytes for the rounds, m = ceil(k/r)) must fit
+ * in RRS_NOALLOC_SCRATCH_BYTES; a larger request is rejected with
+ * RRS_ERR_BUDGET and a message giving both sizes (rrs_last_error).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call clears what must start at zero); calls
+ * whose GPU work overlaps -- other streams or other host threads -- race on
+ * it and must be serialised by the caller.
+ * Errors: INVALID_ARG, BUDGET, UNSUPPORTED, CUDA, INTERNAL.
+ */
+#define RRS_NOALLOC_SCRATCH_BYTES (32u << 20)
+rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int32_t dtype, const void* Z,
+                             int64_t n_queries, int32_t kind, int32_t n_dirs, int32_t n_refinements,
+                             double cap_shrink, uint64_t seed, double* depth_out, int64_t* count_out,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,9 @@ _SIGS = {
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "rrs_profile_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_depth_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
 }
 
 RRS_STAGES = ("prep", "gen", "hd_simt", "hd_tc", "pdap", "argmin")
@@ -193,6 +196,17 @@ def rrs_debug_round_depths(ctx: int, dataset_id: int, Z, n_queries: int, dtype: 
     _check(load().rrs_debug_round_depths(ctx, dataset_id, _ptr(Z), n_queries, dtype, kind, m, _ptr(U), precision,
                                          _ptr(depth_out), _ptr(count_out), _ptr(band_out)),
            "rrs_debug_round_depths")
+
+
+def rrs_depth_noalloc(X, n: int, d: int, dtype: int, Z, n_queries: int, kind: int, n_dirs: int,
+                      n_refinements: int, cap_shrink: float, seed: int, depth_out, count_out=None,
+                      stream=None) -> None:
+    """For callers that cannot allocate device memory: all working memory comes from the
+    library's fixed device array (RRS_NOALLOC_SCRATCH_BYTES); X, Z and the outputs are
+    device pointers; calls must not overlap on the GPU."""
+    _check(load().rrs_depth_noalloc(_ptr(X), n, d, dtype, _ptr(Z), n_queries, kind, n_dirs, n_refinements,
+                                    float(cap_shrink), seed, _ptr(depth_out), _ptr(count_out), _stream(stream)),
+           "rrs_depth_noalloc")
 
 
 def rrs_check(ctx: int, stream=None) -> None:

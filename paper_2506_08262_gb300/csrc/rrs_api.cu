@@ -96,6 +96,8 @@ struct Carve {
 
 }  // namespace
 
+void rrs::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct rrs_ctx {
     int device = 0;
     uint64_t budget = 0;

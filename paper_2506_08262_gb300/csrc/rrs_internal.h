@@ -76,6 +76,9 @@ enum : int {
 __host__ __device__ float band_gamma_fp32(int d);
 float band_gamma_tc(int d);
 
+// Set the text that rrs_last_error() returns on this thread (rrs_api.cu).
+void set_last_error(const char* msg);
+
 // launchers (rrs_kernels.cu)
 cudaError_t launch_prep(const SlotDev* slots, int nslots, const DsDev* ds, float* z32, double* z64,
                         float* poles, cudaStream_t st);
