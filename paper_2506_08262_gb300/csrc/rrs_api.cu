@@ -36,12 +36,16 @@ rrs_status fail(rrs_status st, const char* fmt, ...)
     return st;
 }
 
+// On failure the runtime's pending error is cleared so that it cannot surface
+// in an unrelated later call.
 #define CUDA_TRY(expr)                                                                     \
     do {                                                                                   \
         cudaError_t _e = (expr);                                                           \
-        if (_e != cudaSuccess)                                                             \
+        if (_e != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
             return fail(RRS_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
                         __FILE__, __LINE__);                                               \
+        }                                                                                  \
     } while (0)
 
 // Opt-in host trace (RRS_TRACE=1) for locating failures in the runtime.
@@ -250,7 +254,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
         }
     }
     // shared-memory classes for the selection kernel
-    const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, 227 * 1024};
+    const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
     P.pd_smem.assign(std::begin(classes), std::end(classes));
     P.pd_tasks.assign(P.pd_smem.size(), {});
     struct SlotRounds {

@@ -102,6 +102,7 @@ cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, i
                                    double* X64, float* xnorm, int* bad, cudaStream_t st);
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx);
+size_t pdap_smem_limit();
 int pdap_max_group(int n, int ldx, int m);
 
 // tensor-core path (hd_tc.cu)

@@ -1,7 +1,7 @@
 // RRS round kernels for sm_103a: direction generation (Alg. S1/S4), halfspace
-// counts on the CUDA cores with an exact near-tie recheck (Sec. 2, D_H),
-// projection / asymmetric projection depth by bucket selection (Sec. 2, D_P
-// and D_AP), and the round minimum with the pole update (Alg. 1 steps 4-6).
+// counts on the CUDA cores with an exact near-tie recheck (Sec. 2, D_H), and
+// the round minimum with the pole update (Alg. 1 steps 4-6).  The D_P / D_AP
+// selection kernel lives in pdap.cu.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -338,330 +338,12 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
     const size_t smem = sizeof(float) * ((size_t)(HD_TJ + HD_PC) * max_ldx + HD_PC + HD_TJ);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_hd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
     }
     k_hd_simt<<<ntasks, HD_NT, smem, st>>>(tasks, slots, ds, U, yz, z64, res, band_out, err);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// projection / asymmetric projection depth: keys in shared memory, exact
-// order statistics by bucket selection
-// ---------------------------------------------------------------------------
-
-constexpr int PD_NT = 512;
-constexpr int PD_NW = PD_NT / 32;
-constexpr int PD_NB = 2048;    // histogram bins
-constexpr int PD_CAP = 512;    // candidates gathered for the final ranking
-constexpr int PD_MAXG = 8;
-
-struct SelShared {
-    float fred[PD_NW * 2];
-    int ired[PD_NW];
-    int b1, b2, c1, c2;        // bins of the two ranks and elements below them
-    int nbuf;
-    float v1, v2;
-};
-
-__device__ __forceinline__ float warp_min(float v)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    return v;
-}
-__device__ __forceinline__ int warp_sum(int v)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-__device__ void block_minmax(float& lo, float& hi, SelShared* sh)
-{
-    lo = warp_min(lo);
-    hi = warp_max(hi);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) {
-        sh->fred[w] = lo;
-        sh->fred[PD_NW + w] = hi;
-    }
-    __syncthreads();
-    lo = sh->fred[0];
-    hi = sh->fred[PD_NW];
-    for (int i = 1; i < PD_NW; ++i) {
-        lo = fminf(lo, sh->fred[i]);
-        hi = fmaxf(hi, sh->fred[PD_NW + i]);
-    }
-}
-
-__device__ int block_sum(int v, SelShared* sh)
-{
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh->ired[w] = v;
-    __syncthreads();
-    int s = 0;
-    for (int i = 0; i < PD_NW; ++i) s += sh->ired[i];
-    return s;
-}
-
-__device__ __forceinline__ int bucket_of(float a, float lo, float scale)
-{
-    const int b = __float2int_rz(__fmul_rn(__fsub_rn(a, lo), scale));
-    return b < PD_NB - 1 ? b : PD_NB - 1;
-}
-
-// Values of 0-based ranks q1 <= q2 among the L values f(0..L-1), all of which
-// lie in [lo, hi].  Exact: bucket indices are a monotone function of the
-// value, so every bucket holds a contiguous run of ranks.
-template <class F>
-__device__ void select_ranks(F f, int L, int q1, int q2, float lo, float hi, unsigned* hist, float* buf,
-                             SelShared* sh, float& v1, float& v2, int* err)
-{
-    const int tid = threadIdx.x;
-    int below = 0;
-    for (int iter = 0; iter < 24; ++iter) {
-        if (!(lo < hi)) {
-            v1 = v2 = lo;
-            return;
-        }
-        float scale = __fdiv_rn((float)PD_NB, __fsub_rn(hi, lo));
-        if (!(scale <= FLT_MAX)) scale = FLT_MAX;
-        for (int b = tid; b < PD_NB; b += PD_NT) hist[b] = 0u;
-        __syncthreads();
-        for (int i = tid; i < L; i += PD_NT) {
-            const float a = f(i);
-            if (a >= lo && a <= hi) atomicAdd(&hist[bucket_of(a, lo, scale)], 1u);
-        }
-        __syncthreads();
-        // exclusive scan of the histogram; thread t owns bins [4t, 4t+4)
-        const int r1 = q1 - below, r2 = q2 - below;
-        {
-            unsigned h0 = hist[4 * tid], h1 = hist[4 * tid + 1], h2 = hist[4 * tid + 2], h3 = hist[4 * tid + 3];
-            int own = (int)(h0 + h1 + h2 + h3);
-            int incl = own;
-            const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane == 31) sh->ired[w] = incl;
-            __syncthreads();
-            int base = 0;
-            for (int i = 0; i < w; ++i) base += sh->ired[i];
-            int c = base + incl - own;
-            const unsigned hh[4] = {h0, h1, h2, h3};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int h = (int)hh[k];
-                if (h > 0) {
-                    if (c <= r1 && r1 < c + h) { sh->b1 = 4 * tid + k; sh->c1 = c; }
-                    if (c <= r2 && r2 < c + h) { sh->b2 = 4 * tid + k; sh->c2 = c; }
-                }
-                c += h;
-            }
-            if (tid == 0) sh->nbuf = 0;
-        }
-        __syncthreads();
-        const int b1 = sh->b1, b2 = sh->b2, c1 = sh->c1, c2 = sh->c2;
-        const int cnt = c2 + (int)hist[b2] - c1;
-        if (cnt <= PD_CAP) {
-            for (int i = tid; i < L; i += PD_NT) {
-                const float a = f(i);
-                if (a >= lo && a <= hi) {
-                    const int b = bucket_of(a, lo, scale);
-                    if (b >= b1 && b <= b2) buf[atomicAdd(&sh->nbuf, 1)] = a;
-                }
-            }
-            __syncthreads();
-            const int s1 = r1 - c1, s2 = r2 - c1;
-            for (int t = tid; t < cnt; t += PD_NT) {
-                const float v = buf[t];
-                int nlt = 0, nle = 0;
-                for (int s = 0; s < cnt; ++s) {
-                    const float w2 = buf[s];
-                    nlt += (w2 < v);
-                    nle += (w2 <= v);
-                }
-                if (nlt <= s1 && s1 < nle) sh->v1 = v;
-                if (nlt <= s2 && s2 < nle) sh->v2 = v;
-            }
-            __syncthreads();
-            v1 = sh->v1;
-            v2 = sh->v2;
-            __syncthreads();
-            return;
-        }
-        // too many candidates: narrow the range to buckets b1..b2 and repeat
-        float nlo = FLT_MAX, nhi = -FLT_MAX;
-        for (int i = tid; i < L; i += PD_NT) {
-            const float a = f(i);
-            if (a >= lo && a <= hi) {
-                const int b = bucket_of(a, lo, scale);
-                if (b >= b1 && b <= b2) {
-                    nlo = fminf(nlo, a);
-                    nhi = fmaxf(nhi, a);
-                }
-            }
-        }
-        block_minmax(nlo, nhi, sh);
-        below += c1;
-        lo = nlo;
-        hi = nhi;
-        __syncthreads();
-    }
-    if (tid == 0) atomicOr(err, ERR_SELECT_ITER);
-    v1 = v2 = __int_as_float(0x7FC00000);
-}
-
-size_t pdap_smem_bytes(int n, int group, int ldx)
-{
-    return sizeof(float) * ((((size_t)group * n + 3) & ~(size_t)3) + (size_t)group * ldx + PD_CAP) +
-           sizeof(unsigned) * PD_NB + sizeof(float) * 2 * PD_MAXG + 64;
-}
-
-int pdap_max_group(int n, int ldx, int m)
-{
-    // prefer two resident CTAs per SM (up to 110 KB each), else one (227 KB)
-    const size_t two = 110 * 1024, one = 227 * 1024;
-    int best = 0;
-    for (int g = 1; g <= PD_MAXG && g <= m; ++g)
-        if (pdap_smem_bytes(n, g, ldx) <= two) best = g;
-    if (best == 0 && pdap_smem_bytes(n, 1, ldx) <= one) best = 1;
-    return best;
-}
-
-__global__ void __launch_bounds__(PD_NT) k_pdap(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
-                                                const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
-{
-    extern __shared__ __align__(16) float sm[];
-    __shared__ SelShared sh;
-    const TaskDev T = tasks[blockIdx.x];
-    const SlotDev& S = slots[T.slot];
-    const DsDev D = dsets[S.ds];
-    const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = (d + 3) & ~3;
-    const int G = T.nj;
-    float* keys = sm;                                // G x n (region padded to a float4 multiple)
-    float* uS = keys + (((size_t)G * n + 3) & ~(size_t)3);   // G x ldx, 16-byte aligned
-    float* buf = uS + (size_t)G * ldx;               // PD_CAP
-    unsigned* hist = reinterpret_cast<unsigned*>(buf + PD_CAP);   // PD_NB
-    float* mm = reinterpret_cast<float*>(hist + PD_NB);           // 2 x PD_MAXG
-    const int tid = threadIdx.x;
-
-    for (int e = tid; e < G * ldx; e += PD_NT) uS[e] = U[S.uoff + (int64_t)T.j0 * ldx + e];
-    __syncthreads();
-
-    float lo[PD_MAXG], hi[PD_MAXG];
-#pragma unroll
-    for (int g = 0; g < PD_MAXG; ++g) {
-        lo[g] = FLT_MAX;
-        hi[g] = -FLT_MAX;
-    }
-    for (int i = tid; i < n; i += PD_NT) {
-        const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-        float acc[PD_MAXG];
-#pragma unroll
-        for (int g = 0; g < PD_MAXG; ++g) acc[g] = 0.0f;
-        for (int l = 0; l < dp4; l += 4) {
-            const float4 x = xr[l >> 2];
-#pragma unroll
-            for (int g = 0; g < PD_MAXG; ++g) {
-                if (g < G) {
-                    const float4 u = *reinterpret_cast<const float4*>(uS + g * ldx + l);
-                    acc[g] = fmaf(u.x, x.x, acc[g]);
-                    acc[g] = fmaf(u.y, x.y, acc[g]);
-                    acc[g] = fmaf(u.z, x.z, acc[g]);
-                    acc[g] = fmaf(u.w, x.w, acc[g]);
-                }
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < PD_MAXG; ++g) {
-            if (g < G) {
-                keys[(size_t)g * n + i] = acc[g];
-                lo[g] = fminf(lo[g], acc[g]);
-                hi[g] = fmaxf(hi[g], acc[g]);
-            }
-        }
-    }
-#pragma unroll
-    for (int g = 0; g < PD_MAXG; ++g) {
-        if (g < G) {
-            block_minmax(lo[g], hi[g], &sh);
-            if (tid == 0) {
-                mm[2 * g] = lo[g];
-                mm[2 * g + 1] = hi[g];
-            }
-        }
-    }
-    __syncthreads();
-
-    const int k1 = (n - 1) / 2, k2 = n / 2;
-    for (int g = 0; g < G; ++g) {
-        const float* y = keys + (size_t)g * n;
-        const float ylo = mm[2 * g], yhi = mm[2 * g + 1];
-        float m1, m2;
-        select_ranks([&](int i) { return y[i]; }, n, k1, k2, ylo, yhi, hist, buf, &sh, m1, m2, err);
-        const double med = ((double)m1 + (double)m2) * 0.5;
-        // y_z with exactly the arithmetic of the data projections, so a query equal to a data
-        // point projects to the same FP32 value as that point
-        float yzf = 0.0f;
-        {
-            const float* zr = z32 + S.zoff32;
-            for (int l = 0; l < dp4; l += 4) {
-                yzf = fmaf(uS[g * ldx + l + 0], zr[l + 0], yzf);
-                yzf = fmaf(uS[g * ldx + l + 1], zr[l + 1], yzf);
-                yzf = fmaf(uS[g * ldx + l + 2], zr[l + 2], yzf);
-                yzf = fmaf(uS[g * ldx + l + 3], zr[l + 3], yzf);
-            }
-        }
-        const double yzv = (double)yzf;
-        double depth;
-        if (S.kind == 1) {
-            auto dev = [&](int i) { return __double2float_rn(fabs((double)y[i] - med)); };
-            const float dhi = fmaxf(__double2float_rn(fabs((double)ylo - med)), __double2float_rn(fabs((double)yhi - med)));
-            float a1, a2;
-            select_ranks(dev, n, k1, k2, 0.0f, dhi, hist, buf, &sh, a1, a2, err);
-            const double mad = ((double)a1 + (double)a2) * 0.5;
-            const double num = fabs(yzv - med);
-            depth = (mad == 0.0) ? (num == 0.0 ? 1.0 : 0.0) : 1.0 / (1.0 + num / mad);
-        } else {
-            int cpos = 0;
-            for (int i = tid; i < n; i += PD_NT) cpos += ((double)y[i] > med);
-            const int npos = block_sum(cpos, &sh);
-            double madp = 0.0;
-            if (npos > 0) {
-                const int base = n - npos;
-                float p1, p2;
-                select_ranks([&](int i) { return y[i]; }, n, base + (npos - 1) / 2, base + npos / 2, ylo, yhi, hist,
-                             buf, &sh, p1, p2, err);
-                madp = (((double)p1 - med) + ((double)p2 - med)) * 0.5;
-            }
-            const double num = yzv - med > 0.0 ? yzv - med : 0.0;
-            depth = (madp == 0.0) ? (num == 0.0 ? 1.0 : 0.0) : 1.0 / (1.0 + num / madp);
-        }
-        if (tid == 0) res[S.roff + T.j0 + g] = ResDev{depth, -1};
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
-                        const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
-{
-    if (ntasks <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_pdap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_pdap<<<ntasks, PD_NT, smem, st>>>(tasks, slots, ds, U, z32, res, err);
     return cudaGetLastError();
 }
 

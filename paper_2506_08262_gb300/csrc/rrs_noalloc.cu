@@ -234,7 +234,10 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
 #define NA_TRY(expr)                                                                                 \
     do {                                                                                             \
         cudaError_t _e = (expr);                                                                     \
-        if (_e != cudaSuccess) return noalloc_fail(RRS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+        if (_e != cudaSuccess) {                                                                     \
+            cudaGetLastError();                                                                      \
+            return noalloc_fail(RRS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e));              \
+        }                                                                                            \
     } while (0)
 
     NA_TRY(cudaMemsetAsync(err, 0, 2 * sizeof(int), st));
