@@ -26,7 +26,7 @@
 namespace rrs {
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 512;
 constexpr int NWARP = NT / 32;
 constexpr int NB = 2048;     // buckets per direction
 constexpr int CAP = 256;     // gathered keys per direction and target
@@ -40,12 +40,13 @@ struct Ctl {
     int cnt[MAXG][2];                  // keys in the run
     int fill[MAXG][2];                 // keys gathered so far
     int fb[MAXG];                      // 1: fall back for all statistics, 2: only MAD_+
-    float lo_b[MAXG], scale[MAXG];     // bucket map of the current pass
+    float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: bucket((y - lo_b) * sc_y)
+    float scale[MAXG];                 // sigma_u (or the radius) of each direction
+    float cen[MAXG], sc_d[MAXG];       // bucket map of |y - med| (D_P)
     float v1[MAXG][2], v2[MAXG][2];    // selected order statistics
     float yz[MAXG];
     int nle[MAXG];                     // #(y <= m1)
     int npos[MAXG];                    // #(y > med), D_AP
-    float R;
     int red[NWARP];
     float fred[2 * NWARP];
     // generic fallback
@@ -161,7 +162,10 @@ __device__ void select_generic(F f, int L, int q1, int q2, float lo, float hi, u
                 const float a = f(i);
                 if (a >= lo && a <= hi) {
                     const int b = bucket(a, lo, scale);
-                    if (b >= b1 && b <= b2) buf[atomicAdd(&C.g_n, 1)] = a;
+                    if (b >= b1 && b <= b2) {
+                        const int pos = atomicAdd(&C.g_n, 1);
+                        if (pos < FB_CAP) buf[pos] = a;
+                    }
                 }
             }
             __syncthreads();
@@ -216,17 +220,19 @@ __device__ __forceinline__ double depth_from(double num, double spread)
     return 1.0 / (1.0 + num / spread);
 }
 
-__global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
-                                              const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                              const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
+// G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
+// directions are then held in registers), 0 for any d.
+template <int G, int DP4>
+__global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
+                                                 const DsDev* __restrict__ dsets, const float* __restrict__ U,
+                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ Ctl C;
     const TaskDev T = tasks[blockIdx.x];
     const SlotDev& S = slots[T.slot];
     const DsDev D = dsets[S.ds];
-    const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = (d + 3) & ~3;
-    const int G = T.nj;
+    const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = DP4 ? DP4 : ((d + 3) & ~3);
     const bool ap = (S.kind == 2);
     const int tid = threadIdx.x;
     const int npad = (n + 3) & ~3;
@@ -235,60 +241,108 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
     unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
     float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
 
-    for (int e = tid; e < G * ldx; e += NT) uS[e] = U[S.uoff + (int64_t)T.j0 * ldx + e];
+    const int GA = T.nj;   // live directions; slots GA..G-1 are inert
+    for (int e = tid; e < G * ldx; e += NT) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
+    for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
     if (tid < MAXG * 2) {
         const float qnan = __int_as_float(0x7FC00000);
         C.v1[tid >> 1][tid & 1] = qnan;
         C.v2[tid >> 1][tid & 1] = qnan;
     }
-    if (tid < MAXG) C.npos[tid] = 0;
-    for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
-    // R bounds every |u'x_i|: |u| <= 1 + 2^-20 for the stream's unit vectors
-    float rmax = 0.0f;
-    for (int i = tid; i < n; i += NT) rmax = fmaxf(rmax, D.xnorm[i]);
-    rmax = warp_max(rmax);
-    if ((tid & 31) == 0) C.fred[tid >> 5] = rmax;
-    __syncthreads();
-    if (tid == 0) {
-        float R = 0.0f;
-        for (int i = 0; i < NWARP; ++i) R = fmaxf(R, C.fred[i]);
-        R = R * 1.0001f + 1e-30f;
-        C.R = R;
+    if (tid < MAXG) {
+        C.npos[tid] = 0;
+        C.fb[tid] = tid < GA ? 0 : 3;
     }
+    __syncthreads();
+    // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
+    // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
+    // to the edge buckets, which keeps the bucket map monotone.
     if (tid < G) {
-        // y_z with exactly the arithmetic of the data keys
-        float a = 0.0f;
+        const int g = tid;
+        const float* u = uS + g * ldx;
+        float a = 0.0f, yc = 0.0f;
         const float* zr = z32 + S.zoff32;
-        for (int l = 0; l < dp4; ++l) a = fmaf(uS[tid * ldx + l], zr[l], a);
-        C.yz[tid] = a;
+        for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);   // y_z: same arithmetic as the keys
+        for (int l = 0; l < d; ++l) yc = fmaf(u[l], D.center[l], yc);
+        float half = D.rc * 1.0001f;
+        if (D.cov) {
+            float q = 0.0f;
+            for (int r = 0; r < d; ++r) {
+                float t = 0.0f;
+                for (int c2 = 0; c2 < d; ++c2) t = fmaf(D.cov[r * d + c2], u[c2], t);
+                q = fmaf(u[r], t, q);
+            }
+            const float sg = sqrtf(fmaxf(q, 0.0f));
+            if (sg > 0.0f && 5.0f * sg < half) half = 5.0f * sg;
+            C.scale[g] = sg;   // kept for the deviation range
+        } else {
+            C.scale[g] = half;
+        }
+        if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
+        C.yz[g] = a;
+        C.lo_b[g] = yc - half;
+        C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
     }
     __syncthreads();
-    const float R = C.R;
-    const float sc0 = __fdiv_rn((float)NB, __fadd_rn(R, R));
-    const float lo0 = -R;
 
-    // ---- pass A: keys + bucket counts -----------------------------------------
-    for (int i = tid; i < n; i += NT) {
-        const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-        float acc[MAXG] = {0.f, 0.f, 0.f, 0.f};
-        for (int l = 0; l < dp4; l += 4) {
-            const float4 x = xr[l >> 2];
+    // ---- pass A: keys + bucket counts ----------------------------------------------
+    {
+        float lo[G], sc[G];
 #pragma unroll
-            for (int g = 0; g < MAXG; ++g) {
-                if (g < G) {
-                    const float4 u = *reinterpret_cast<const float4*>(uS + g * ldx + l);
-                    acc[g] = fmaf(u.x, x.x, acc[g]);
-                    acc[g] = fmaf(u.y, x.y, acc[g]);
-                    acc[g] = fmaf(u.z, x.z, acc[g]);
-                    acc[g] = fmaf(u.w, x.w, acc[g]);
+        for (int g = 0; g < G; ++g) {
+            lo[g] = C.lo_b[g];
+            sc[g] = C.sc_y[g];
+        }
+        if (DP4 > 0) {
+            float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
+            for (int i = tid; i < n; i += NT) {
+                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                float acc[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = 0.f;
+#pragma unroll
+                for (int c = 0; c < DP4 / 4; ++c) {
+                    const float4 x = xr[c];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        acc[g] = fmaf(ur[g][c].x, x.x, acc[g]);
+                        acc[g] = fmaf(ur[g][c].y, x.y, acc[g]);
+                        acc[g] = fmaf(ur[g][c].z, x.z, acc[g]);
+                        acc[g] = fmaf(ur[g][c].w, x.w, acc[g]);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    keys[(size_t)g * npad + i] = acc[g];
+                    atomicAdd(&hist[g * NB + bucket(acc[g], lo[g], sc[g])], 1u);
                 }
             }
-        }
+        } else {
+            for (int i = tid; i < n; i += NT) {
+                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                float acc[G];
 #pragma unroll
-        for (int g = 0; g < MAXG; ++g) {
-            if (g < G) {
-                keys[(size_t)g * npad + i] = acc[g];
-                atomicAdd(&hist[g * NB + bucket(acc[g], lo0, sc0)], 1u);
+                for (int g = 0; g < G; ++g) acc[g] = 0.f;
+                for (int l = 0; l < dp4; l += 4) {
+                    const float4 x = xr[l >> 2];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const float4 u = *reinterpret_cast<const float4*>(uS + g * ldx + l);
+                        acc[g] = fmaf(u.x, x.x, acc[g]);
+                        acc[g] = fmaf(u.y, x.y, acc[g]);
+                        acc[g] = fmaf(u.z, x.z, acc[g]);
+                        acc[g] = fmaf(u.w, x.w, acc[g]);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    keys[(size_t)g * npad + i] = acc[g];
+                    atomicAdd(&hist[g * NB + bucket(acc[g], lo[g], sc[g])], 1u);
+                }
             }
         }
     }
@@ -297,7 +351,7 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
     const int k1 = (n - 1) / 2, k2 = n / 2;
     const int npos_guess = (n & 1) ? (n - 1) / 2 : n / 2;
     // ---- bucket runs of the wanted ranks ----------------------------------------
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < GA; ++g) {
         int ba, ca, bb, cb;
         find_buckets(hist + g * NB, k1, k2, C, ba, ca, bb, cb);
         if (tid == 0) {
@@ -333,26 +387,34 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
 
     // ---- pass C: gather the runs ------------------------------------------------
     {
-        int bl0[MAXG], bw0[MAXG], bl1[MAXG], bw1[MAXG];
-        bool on[MAXG];
+        int bl0[G], bw0[G], bl1[G], bw1[G];
+        float lo[G], sc[G];
 #pragma unroll
-        for (int g = 0; g < MAXG; ++g) {
-            on[g] = g < G && !C.fb[g];
-            bl0[g] = g < G ? C.b_lo[g][0] : 0;
-            bw0[g] = g < G ? C.b_hi[g][0] - C.b_lo[g][0] : -1;
-            bl1[g] = (g < G && ap) ? C.b_lo[g][1] : 0;
-            bw1[g] = (g < G && ap) ? C.b_hi[g][1] - C.b_lo[g][1] : -1;
+        for (int g = 0; g < G; ++g) {
+            // a run that is off gets a start no bucket index can reach: (b - start) is then
+            // never <= 0 as an unsigned number
+            const bool on = !C.fb[g];
+            lo[g] = C.lo_b[g];
+            sc[g] = C.sc_y[g];
+            bl0[g] = on ? C.b_lo[g][0] : (1 << 30);
+            bw0[g] = on ? C.b_hi[g][0] - C.b_lo[g][0] : 0;
+            bl1[g] = (ap && on) ? C.b_lo[g][1] : (1 << 30);
+            bw1[g] = (ap && on) ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
         }
         for (int i = tid; i < n; i += NT) {
 #pragma unroll
-            for (int g = 0; g < MAXG; ++g) {
-                if (on[g]) {
+            for (int g = 0; g < G; ++g) {
+                {
                     const float y = keys[(size_t)g * npad + i];
-                    const int b = bucket(y, lo0, sc0);
-                    if ((unsigned)(b - bl0[g]) <= (unsigned)bw0[g])
-                        buf[(g * 2 + 0) * CAP + atomicAdd(&C.fill[g][0], 1)] = y;
-                    if (ap && (unsigned)(b - bl1[g]) <= (unsigned)bw1[g])
-                        buf[(g * 2 + 1) * CAP + atomicAdd(&C.fill[g][1], 1)] = y;
+                    const int b = bucket(y, lo[g], sc[g]);
+                    if ((unsigned)(b - bl0[g]) <= (unsigned)bw0[g]) {
+                        const int pos = atomicAdd(&C.fill[g][0], 1);
+                        if (pos < CAP) buf[(g * 2 + 0) * CAP + pos] = y;
+                    }
+                    if (ap && (unsigned)(b - bl1[g]) <= (unsigned)bw1[g]) {
+                        const int pos = atomicAdd(&C.fill[g][1], 1);
+                        if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = y;
+                    }
                 }
             }
         }
@@ -408,27 +470,31 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
         }
         __syncthreads();
     } else {
-        // ---- D_P: |y - med| histogram, gather, ranks ------------------------------
+        // ---- D_P: |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
         for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
         if (tid < G) {
             const float m = __fmul_rn(__fadd_rn(C.v1[tid][0], C.v2[tid][0]), 0.5f);
-            const float dmax = __fmul_rn(__fadd_rn(R, fabsf(m)), 1.0001f) + 1e-30f;
-            C.lo_b[tid] = m;   // centre
-            C.scale[tid] = __fdiv_rn((float)NB, dmax);
+            float dmax = D.cov ? 4.0f * C.scale[tid] : 0.0f;
+            const float hard = __fmul_rn(__fadd_rn(D.rc, fabsf(m - C.lo_b[tid] - 0.5f * (float)NB / C.sc_y[tid])),
+                                         1.0001f);
+            if (!(dmax > 0.0f) || dmax > hard) dmax = hard;
+            if (!(dmax > 0.0f)) dmax = 1.0f;
+            C.cen[tid] = m;
+            C.sc_d[tid] = __fdiv_rn((float)NB, dmax);
         }
         __syncthreads();
         {
-            float cen[MAXG], scl[MAXG];
-            bool on[MAXG];
+            float cen[G], scl[G];
+            bool on[G];
 #pragma unroll
-            for (int g = 0; g < MAXG; ++g) {
-                on[g] = g < G && !C.fb[g];
-                cen[g] = g < G ? C.lo_b[g] : 0.f;
-                scl[g] = g < G ? C.scale[g] : 0.f;
+            for (int g = 0; g < G; ++g) {
+                on[g] = !C.fb[g];
+                cen[g] = C.cen[g];
+                scl[g] = C.sc_d[g];
             }
             for (int i = tid; i < n; i += NT) {
 #pragma unroll
-                for (int g = 0; g < MAXG; ++g) {
+                for (int g = 0; g < G; ++g) {
                     if (on[g]) {
                         const float dv = fabsf(__fsub_rn(keys[(size_t)g * npad + i], cen[g]));
                         atomicAdd(&hist[g * NB + bucket(dv, 0.0f, scl[g])], 1u);
@@ -452,25 +518,25 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
             __syncthreads();
         }
         {
-            float cen[MAXG], scl[MAXG];
-            int bl[MAXG], bw[MAXG];
-            bool on[MAXG];
+            float cen[G], scl[G];
+            int bl[G], bw[G];
 #pragma unroll
-            for (int g = 0; g < MAXG; ++g) {
-                on[g] = g < G && !C.fb[g];
-                cen[g] = g < G ? C.lo_b[g] : 0.f;
-                scl[g] = g < G ? C.scale[g] : 0.f;
-                bl[g] = g < G ? C.b_lo[g][1] : 0;
-                bw[g] = g < G ? C.b_hi[g][1] - C.b_lo[g][1] : -1;
+            for (int g = 0; g < G; ++g) {
+                cen[g] = C.cen[g];
+                scl[g] = C.sc_d[g];
+                bl[g] = !C.fb[g] ? C.b_lo[g][1] : (1 << 30);
+                bw[g] = !C.fb[g] ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
             }
             for (int i = tid; i < n; i += NT) {
 #pragma unroll
-                for (int g = 0; g < MAXG; ++g) {
-                    if (on[g]) {
+                for (int g = 0; g < G; ++g) {
+                    {
                         const float dv = fabsf(__fsub_rn(keys[(size_t)g * npad + i], cen[g]));
                         const int b = bucket(dv, 0.0f, scl[g]);
-                        if ((unsigned)(b - bl[g]) <= (unsigned)bw[g])
-                            buf[(g * 2 + 1) * CAP + atomicAdd(&C.fill[g][1], 1)] = dv;
+                        if ((unsigned)(b - bl[g]) <= (unsigned)bw[g]) {
+                            const int pos = atomicAdd(&C.fill[g][1], 1);
+                            if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = dv;
+                        }
                     }
                 }
             }
@@ -493,11 +559,32 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
     // ---- fallback directions: iterated bucket selection over their keys ---------
     for (int g = 0; g < G; ++g) {
         const int fb = C.fb[g];
-        if (!fb) continue;
+        if (fb == 0 || fb == 3) continue;
         const float* y = keys + (size_t)g * npad;
+        // exact range of this direction's keys
+        float kl = FLT_MAX, kh = -FLT_MAX;
+        for (int i = tid; i < n; i += NT) {
+            kl = fminf(kl, y[i]);
+            kh = fmaxf(kh, y[i]);
+        }
+        kl = warp_min(kl);
+        kh = warp_max(kh);
+        __syncthreads();
+        if ((tid & 31) == 0) {
+            C.fred[tid >> 5] = kl;
+            C.fred[NWARP + (tid >> 5)] = kh;
+        }
+        __syncthreads();
+        kl = C.fred[0];
+        kh = C.fred[NWARP];
+        for (int i = 1; i < NWARP; ++i) {
+            kl = fminf(kl, C.fred[i]);
+            kh = fmaxf(kh, C.fred[NWARP + i]);
+        }
+        __syncthreads();
         float m1, m2;
         if (fb == 1) {
-            select_generic([&](int i) { return y[i]; }, n, k1, k2, lo0, R, hist, buf, C, m1, m2, err);
+            select_generic([&](int i) { return y[i]; }, n, k1, k2, kl, kh, hist, buf, C, m1, m2, err);
             if (tid == 0) {
                 C.v1[g][0] = m1;
                 C.v2[g][0] = m2;
@@ -521,7 +608,7 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
             if (tid == 0) C.npos[g] = npos;
             float p1 = m1, p2 = m1;
             if (npos > 0)
-                select_generic([&](int i) { return y[i]; }, n, nle + (npos - 1) / 2, nle + npos / 2, lo0, R, hist,
+                select_generic([&](int i) { return y[i]; }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, hist,
                                buf, C, p1, p2, err);
             if (tid == 0) {
                 C.v1[g][1] = p1;
@@ -529,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
             }
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
-            const float dmax = __fmul_rn(__fadd_rn(R, fabsf(m)), 1.0001f) + 1e-30f;
+            const float dmax = fmaxf(fabsf(__fsub_rn(kl, m)), fabsf(__fsub_rn(kh, m)));
             float a1, a2;
             select_generic([&](int i) { return fabsf(__fsub_rn(y[i], m)); }, n, k1, k2, 0.0f, dmax, hist, buf, C, a1,
                            a2, err);
@@ -542,13 +629,12 @@ __global__ void __launch_bounds__(NT) k_pdap2(const TaskDev* __restrict__ tasks,
     }
 
     // ---- depths (FP64 on a handful of values) --------------------------------------
-    if (tid < G) {
+    if (tid < GA) {
         const int g = tid;
         const double med = ((double)C.v1[g][0] + (double)C.v2[g][0]) * 0.5;
         const double yzv = (double)C.yz[g];
         double depth;
         if (ap) {
-            // MAD_+ = mean of the two middle positive deviations (0 if there are none)
             const double madp =
                 C.npos[g] > 0 ? (((double)C.v1[g][1] - med) + ((double)C.v2[g][1] - med)) * 0.5 : 0.0;
             depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
@@ -577,10 +663,11 @@ size_t pdap_smem_limit()
 
 int pdap_max_group(int n, int ldx, int m)
 {
-    // largest G <= 4 that fits one CTA per SM, preferring two CTAs per SM when G >= 2 fits there
+    // G in {1, 2, 4}: the largest that fits two CTAs per SM when that is at least 2, else the
+    // largest that fits one CTA per SM
     const size_t one = pdap_smem_limit(), two = 110 * 1024;
     int g_one = 0, g_two = 0;
-    for (int g = 1; g <= MAXG && g <= m; ++g) {
+    for (int g = 1; g <= MAXG && g <= m; g *= 2) {
         if (pdap_smem_bytes(n, g, ldx) <= one) g_one = g;
         if (pdap_smem_bytes(n, g, ldx) <= two) g_two = g;
     }
@@ -588,18 +675,49 @@ int pdap_max_group(int n, int ldx, int m)
     return g_one;
 }
 
-cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
-                        const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+template <int G, int DP4>
+static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
+                            const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
 {
-    if (ntasks <= 0) return cudaSuccess;
-    if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_pdap2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_pdap2<G, DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<<<ntasks, NT, smem, st>>>(tasks, slots, ds, U, z32, res, err);
+    k_pdap2<G, DP4><<<ntasks, NT, smem, st>>>(tasks, slots, ds, U, z32, res, err);
     return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t launch_g(int dp4, const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots,
+                            const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+{
+    switch (dp4) {
+    case 4: return launch_t<G, 4>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 8: return launch_t<G, 8>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 12: return launch_t<G, 12>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 16: return launch_t<G, 16>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    default: return launch_t<G, 0>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    }
+}
+
+int pdap_dp4_class(int d)
+{
+    const int dp4 = (d + 3) & ~3;
+    return dp4 <= 16 ? dp4 : 0;
+}
+
+cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
+                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
+    switch (group) {
+    case 1: return launch_g<1>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 2: return launch_g<2>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 4: return launch_g<4>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace rrs

@@ -14,6 +14,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rrs.h"
@@ -80,6 +81,9 @@ struct Dataset {
     double* X64 = nullptr;
     float* xnorm = nullptr;
     uint16_t* Xbf = nullptr;
+    float* center = nullptr;   // d, then (d <= RRS_COV_MAX_D) d*d covariance, then the radius
+    float* cov = nullptr;
+    float rc = 0.0f;
     size_t bytes = 0;
 };
 
@@ -176,8 +180,9 @@ struct Plan {
     std::vector<DsDev> ds;
     std::vector<SlotDev> slots;
     std::vector<TaskDev> gen_tasks, hd_tasks;
-    std::vector<std::vector<TaskDev>> pd_tasks;       // one list per shared-memory class
-    std::vector<size_t> pd_smem;                      // bytes of each class
+    std::vector<std::vector<TaskDev>> pd_tasks;       // one list per (shared-memory class, group, d class)
+    std::vector<size_t> pd_smem;                      // bytes of each list's class
+    std::vector<int> pd_group, pd_dp4;
     std::vector<int32_t> argmin_list;
     // active prefix lengths per round
     std::vector<int> n_gen, n_hd, n_arg;
@@ -249,14 +254,28 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             dd.d = D.d;
             dd.ldx = D.ldx;
             dd.kp = D.kp;
+            dd.center = D.center;
+            dd.cov = D.cov;
+            dd.rc = D.rc;
             dsidx[R.dset] = (int)P.ds.size();
             P.ds.push_back(dd);
         }
     }
     // shared-memory classes for the selection kernel
     const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
-    P.pd_smem.assign(std::begin(classes), std::end(classes));
-    P.pd_tasks.assign(P.pd_smem.size(), {});
+    std::map<std::tuple<size_t, int, int>, int> pd_index;
+    auto pd_list = [&](size_t smem, int group, int dp4) {
+        auto key = std::make_tuple(smem, group, dp4);
+        auto it = pd_index.find(key);
+        if (it != pd_index.end()) return it->second;
+        const int idx = (int)P.pd_tasks.size();
+        pd_index[key] = idx;
+        P.pd_tasks.emplace_back();
+        P.pd_smem.push_back(smem);
+        P.pd_group.push_back(group);
+        P.pd_dp4.push_back(dp4);
+        return idx;
+    };
     struct SlotRounds {
         int r;
     };
@@ -277,11 +296,12 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
                             "projection depth needs n*4 bytes of shared memory per direction; n=%lld is too large",
                             (long long)D.n);
             const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
-            for (size_t c = 0; c < P.pd_smem.size(); ++c)
-                if (need <= P.pd_smem[c]) {
-                    cls = (int)c;
+            for (size_t c : classes)
+                if (need <= c) {
+                    cls = pd_list(c, G, pdap_dp4_class(D.d));
                     break;
                 }
+            if (cls < 0) return fail(RRS_ERR_INTERNAL, "no shared-memory class for n=%lld", (long long)D.n);
         }
         for (int64_t q = 0; q < R.nq; ++q) {
             SlotDev S{};
@@ -418,7 +438,8 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
         for (size_t c = 0; c < P.pd_tasks.size(); ++c) {
             if (P.n_pd[c][l] > 0) {
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
-                CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.d_slots, P.d_ds, P.U, P.z32, P.res,
+                CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_dp4[c], P.d_slots,
+                                     P.d_ds, P.U, P.z32, P.res,
                                      ctx->d_err, st));
                 ctx->launches++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
@@ -499,6 +520,7 @@ rrs_status rrs_destroy(rrs_ctx* ctx)
         cudaFree(kv.second.X64);
         cudaFree(kv.second.xnorm);
         cudaFree(kv.second.Xbf);
+        cudaFree(kv.second.center);
     }
     for (auto& g : ctx->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -529,7 +551,9 @@ rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t 
     const size_t esz = dtype == RRS_F32 ? 4 : 8;
     const size_t b32 = sizeof(float) * (size_t)n * D.ldx, b64 = dtype == RRS_F64 ? sizeof(double) * n * d : 0,
                  bn = sizeof(float) * n;
-    D.bytes = b32 + b64 + bn;
+    const bool want_cov = d <= RRS_COV_MAX_D;
+    const size_t bmom = sizeof(float) * ((size_t)d + (want_cov ? (size_t)d * d : 0) + 1);
+    D.bytes = b32 + b64 + bn + bmom;
     if (!budget_ok(ctx, D.bytes)) return fail(RRS_ERR_BUDGET, "dataset needs %zu bytes", D.bytes);
     void* staged = nullptr;
     const void* src = X;
@@ -542,17 +566,27 @@ rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t 
     cudaError_t e = cudaMalloc(&D.X32, b32);
     if (e == cudaSuccess && b64) e = cudaMalloc(&D.X64, b64);
     if (e == cudaSuccess) e = cudaMalloc(&D.xnorm, bn);
+    if (e == cudaSuccess) e = cudaMalloc(&D.center, bmom);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_convert_dataset(src, dtype, n, d, D.ldx, D.X32, D.X64, D.xnorm, ctx->d_err, st);
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&bad, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     ctx->launches++;
+    if (e == cudaSuccess && !bad) {
+        D.cov = want_cov ? D.center + d : nullptr;
+        float* rc_dev = D.center + d + (want_cov ? (size_t)d * d : 0);
+        e = launch_moments(D.X32, n, d, D.ldx, D.center, D.cov, rc_dev, st);
+        if (e == cudaSuccess) e = cudaMemcpy(&D.rc, rc_dev, sizeof(float), cudaMemcpyDeviceToHost);
+        ctx->launches += 3;
+    }
     cudaFree(staged);
     if (e != cudaSuccess || bad) {
+        cudaGetLastError();
         cudaFree(D.X32);
         cudaFree(D.X64);
         cudaFree(D.xnorm);
+        cudaFree(D.center);
         if (e != cudaSuccess) return fail(RRS_ERR_CUDA, "dataset upload failed: %s", cudaGetErrorString(e));
         return fail(RRS_ERR_INVALID_ARG, "X holds a non-finite value or one of magnitude >= 2^64");
     }
@@ -575,6 +609,7 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id)
     cudaFree(it->second.X64);
     cudaFree(it->second.xnorm);
     cudaFree(it->second.Xbf);
+    cudaFree(it->second.center);
     ctx->used -= it->second.bytes;
     ctx->datasets.erase(it);
     return RRS_OK;
@@ -884,7 +919,8 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
         } else {
             for (size_t c = 0; c < P.pd_tasks.size(); ++c)
                 if (!P.pd_tasks[c].empty())
-                    CUDA_TRY(launch_pdap(P.d_pd[c], (int)P.pd_tasks[c].size(), P.pd_smem[c], P.d_slots, P.d_ds, P.U,
+                    CUDA_TRY(launch_pdap(P.d_pd[c], (int)P.pd_tasks[c].size(), P.pd_smem[c], P.pd_group[c],
+                                         P.pd_dp4[c], P.d_slots, P.d_ds, P.U,
                                          P.z32, P.res, ctx->d_err, st));
         }
         ctx->launches += 4;

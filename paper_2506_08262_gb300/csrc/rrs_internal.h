@@ -13,12 +13,16 @@ struct DsDev {
     const double* X64;     // n x d FP64 rows, or nullptr if the data came in FP32
     const float* xnorm;    // n Euclidean row norms, rounded up
     const uint16_t* Xbf;   // n x (2*kp) BF16 planes [x_hi | x_lo] for the tensor-core path, or nullptr
+    const float* center;   // d: mean of the rows
+    const float* cov;      // d x d covariance of the rows (d <= RRS_COV_MAX_D), else nullptr
     int64_t n;
     int32_t d;
     int32_t ldx;           // padded FP32 row stride (floats)
     int32_t kp;            // padded K of one BF16 plane (multiple of 64), 0 if no planes
-    int32_t pad;
+    float rc;              // max_i |x_i - center| (rounded up): every |u'(x_i - center)| <= rc for |u| <= 1
 };
+
+constexpr int RRS_COV_MAX_D = 128;
 
 // One query of a launch (any request, any dataset).
 struct SlotDev {
@@ -87,8 +91,10 @@ cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, c
 cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const SlotDev* slots, const DsDev* ds,
                            const float* U, const double* yz, const double* z64, ResDev* res, int64_t* band_out,
                            int* err, cudaStream_t st);
-cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
-                        const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st);
+// group: directions per CTA (1, 2 or 4, from pdap_max_group); dp4: pdap_dp4_class(d), shared by every task
+cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
+                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st);
+int pdap_dp4_class(int d);
 cudaError_t launch_argmin(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
                           const ResDev* res, const float* poles_cur, float* poles_next, int round0,
                           int last_round, cudaStream_t st);
@@ -100,6 +106,9 @@ cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, fl
                               float* U, cudaStream_t st);
 cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, int ldx, float* X32,
                                    double* X64, float* xnorm, int* bad, cudaStream_t st);
+// mean, covariance (d <= RRS_COV_MAX_D) and radius about the mean of the FP32 rows; rc_out is a device float
+cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* center, float* cov, float* rc_out,
+                           cudaStream_t st);
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx);
 size_t pdap_smem_limit();

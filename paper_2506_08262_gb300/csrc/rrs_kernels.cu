@@ -61,6 +61,73 @@ cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, i
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// data moments (range heuristics of the selection kernel only; no result
+// depends on their accuracy)
+// ---------------------------------------------------------------------------
+
+__global__ void k_center(const float* __restrict__ X32, int64_t n, int ldx, float* __restrict__ center)
+{
+    const int a = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)X32[i * ldx + a];
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) center[a] = (float)(red[0] / (double)n);
+}
+
+__global__ void k_cov(const float* __restrict__ X32, int64_t n, int d, int ldx, const float* __restrict__ center,
+                      float* __restrict__ cov)
+{
+    const int a = blockIdx.x / d, b = blockIdx.x % d;
+    if (b < a) return;
+    const float ca = center[a], cb = center[b];
+    float s = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fmaf(X32[i * ldx + a] - ca, X32[i * ldx + b] - cb, s);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float v = red[0] / (float)n;
+        cov[a * d + b] = v;
+        cov[b * d + a] = v;
+    }
+}
+
+__global__ void k_radius(const float* __restrict__ X32, int64_t n, int d, int ldx, const float* __restrict__ center,
+                         float* rc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int l = 0; l < d; ++l) {
+        const double v = (double)X32[i * ldx + l] - (double)center[l];
+        s = __fma_rn(v, v, s);
+    }
+    const float r = __double2float_ru(__dsqrt_ru(s) * (1.0 + 1e-9));
+    atomicMax((int*)rc, __float_as_int(r));   // non-negative floats order like their bit patterns
+}
+
+cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* center, float* cov, float* rc_out,
+                           cudaStream_t st)
+{
+    k_center<<<d, 256, 0, st>>>(X32, n, ldx, center);
+    if (cov) k_cov<<<d * d, 256, 0, st>>>(X32, n, d, ldx, center, cov);
+    cudaError_t e = cudaMemsetAsync(rc_out, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    k_radius<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(X32, n, d, ldx, center, rc_out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_check_finite(const T* __restrict__ Z, int64_t count, int* bad)
 {

@@ -78,7 +78,7 @@ int padded_stride(int d)
 }
 
 struct Layout {
-    size_t ds, x32, xnorm, slots, gen, hd, pd, arg, z32, poles, z64, U, yz, res, err, total;
+    size_t ds, x32, xnorm, mom, slots, gen, hd, pd, arg, z32, poles, z64, U, yz, res, err, total;
 };
 
 Layout layout(int64_t n, int ldx, int d, int64_t nq, int m, int gen_per, int hd_per, int pd_per)
@@ -93,6 +93,7 @@ Layout layout(int64_t n, int ldx, int d, int64_t nq, int m, int gen_per, int hd_
     L.ds = take(sizeof(DsDev));
     L.x32 = take(sizeof(float) * (size_t)n * ldx);
     L.xnorm = take(sizeof(float) * (size_t)n);
+    L.mom = take(sizeof(float) * ((size_t)d + (d <= RRS_COV_MAX_D ? (size_t)d * d : 0) + 1));
     L.slots = take(sizeof(SlotDev) * (size_t)nq);
     L.gen = take(sizeof(TaskDev) * (size_t)nq * gen_per);
     L.hd = take(sizeof(TaskDev) * (size_t)nq * hd_per);
@@ -110,7 +111,8 @@ Layout layout(int64_t n, int ldx, int d, int64_t nq, int m, int gen_per, int hd_
 }
 
 // Launch tables and per-query slots, written on the device (no host tables).
-__global__ void k_noalloc_plan(DsDev* ds, const float* X32, const double* X64, const float* xnorm, int64_t n, int d,
+__global__ void k_noalloc_plan(DsDev* ds, const float* X32, const double* X64, const float* xnorm,
+                               const float* center, const float* cov, const float* rc, int64_t n, int d,
                                int ldx, SlotDev* slots, TaskDev* gen, TaskDev* hd, TaskDev* pd, int32_t* arg,
                                int64_t nq, int kind, int m, int r, float alpha, uint64_t seed, const void* Z,
                                int zdtype, double* depth_out, int64_t* count_out, int gen_per, int hd_per,
@@ -127,6 +129,9 @@ __global__ void k_noalloc_plan(DsDev* ds, const float* X32, const double* X64, c
         D.d = d;
         D.ldx = ldx;
         D.kp = 0;
+        D.center = center;
+        D.cov = cov;
+        D.rc = *rc;
         *ds = D;
     }
     if (q >= nq) return;
@@ -244,9 +249,13 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     const double* X64 = dtype == RRS_F64 ? (const double*)X : nullptr;
     NA_TRY(launch_convert_dataset(X, dtype, n, d, ldx, X32, nullptr, xnorm, err, st));
     NA_TRY(launch_check_finite(Z, dtype, n_queries * d, err, st));
+    float* center = (float*)(B + L.mom);
+    float* cov = d <= RRS_COV_MAX_D ? center + d : nullptr;
+    float* rc = center + d + (d <= RRS_COV_MAX_D ? (size_t)d * d : 0);
+    NA_TRY(launch_moments(X32, n, d, ldx, center, cov, rc, st));
     const int nt = 128;
     k_noalloc_plan<<<(unsigned)((n_queries + nt - 1) / nt), nt, 0, st>>>(
-        ds, X32, X64, xnorm, n, d, ldx, slots, gen, hd, pd, arg, n_queries, kind, m, n_refinements,
+        ds, X32, X64, xnorm, center, cov, rc, n, d, ldx, slots, gen, hd, pd, arg, n_queries, kind, m, n_refinements,
         (float)cap_shrink, seed, Z, dtype, depth_out, count_out, gen_per, hd_per, hd_size, pd_per, G);
     NA_TRY(cudaGetLastError());
     int bad = 0;
@@ -264,7 +273,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
         if (kind == RRS_HALFSPACE)
             NA_TRY(launch_hd_simt(hd, nq * hd_per, ldx, slots, ds, U, yz, z64, res, nullptr, err + 1, st));
         else
-            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, slots, ds, U, z32, res, err + 1, st));
+            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, G, pdap_dp4_class(d), slots, ds, U, z32, res, err + 1, st));
         NA_TRY(launch_argmin(slots, arg, nq, U, res, cur, nxt, l, 0, st));
     }
     int flags = 0;
