@@ -1,20 +1,475 @@
-// Tensor-core halfspace path (placeholder until the tcgen05 kernel lands).
+// Halfspace depth counts on the tcgen05 tensor cores (Sec. 2, D_H; the projection
+// Y = U X^T of Sec. 4.1 as a GEMM) with split-BF16x3 products.
+//
+// Every x and u is split into BF16 parts, x = x_hi + x_lo (+ residual), and
+// u'x is formed as u_hi'x_hi + u_lo'x_hi + u_hi'x_lo with FP32 accumulation in
+// tensor memory.  The query's projection is folded into the same GEMM: the
+// data planes carry 1 in two spare K columns and the direction planes carry
+// the BF16 parts of -u'z there, so the accumulator holds t = u'x - u'z
+// directly.  The epilogue counts t < -b and t > b, b = gamma (|x| + |z|) a
+// bound on the error of t, and re-checks every |t| <= b with the exact FP64
+// sign test, so the counts are exact.
+//
+// CTA layout (192 threads): warp 0 streams point tiles with TMA into a
+// 4-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-5 read
+// the accumulator (one direction per TMEM lane) and count.  The accumulator is
+// double buffered so the epilogue of tile t overlaps the MMAs of tile t+1.
+// Every wait on an mbarrier is bounded; on timeout the CTA flags ERR_TIMEOUT
+// and winds down.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "rrs_device.cuh"
 #include "rrs_internal.h"
 
 namespace rrs {
 
-float band_gamma_tc(int d) { (void)d; return 1e-4f; }
-bool hd_tc_supported(int d) { (void)d; return false; }
+namespace {
 
-cudaError_t launch_build_bf16_planes(const float*, int64_t, int, int, int, uint16_t*, cudaStream_t)
+constexpr int BM = 128;          // directions per CTA (TMEM lanes)
+constexpr int BN = 128;          // points per tile (accumulator columns)
+constexpr int STAGES = 4;
+constexpr int NTHREADS = 192;
+
+__host__ __device__ constexpr int plane_bytes_rows(int rows) { return rows * 128; }   // one 64-wide K chunk
+
+// instruction descriptor of tcgen05.mma kind::f16: BF16 A and B, FP32 accumulator,
+// both operands K-major, M = 128, N = BN
+constexpr uint32_t kIdesc = (1u << 4)                 // D format: FP32
+                            | (1u << 7)               // A format: BF16
+                            | (1u << 10)              // B format: BF16
+                            | ((uint32_t)(BN >> 3) << 17)
+                            | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 bytes
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
-    return cudaErrorNotSupported;
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // layout: 128-byte swizzle
+    return d;
 }
 
-cudaError_t launch_hd_tc(const TaskDev*, int, const SlotDev*, const DsDev*, const float*, const double*,
-                         const double*, ResDev*, int64_t*, int*, cudaStream_t)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
-    return cudaErrorNotSupported;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity to complete: gives up after
+// about a second of SM clock, or as soon as any CTA of the grid has flagged a
+// timeout in the shared error word.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int* err, bool honor_grid_abort = true)
+{
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if ((i & 255u) == 255u) {
+            if (clock64() - t0 > 2000000000LL) return false;
+            if (honor_grid_abort && (*(volatile const int*)err & ERR_TIMEOUT)) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) in a K chunk of 64 BF16 per row, 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k)
+{
+    const int unit = (k >> 3) ^ (row & 7);
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + unit * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+struct TcShared {
+    uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+    int mma_tiles;   // tiles whose operands the MMA issuer has consumed
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_hd_tc(const __grid_constant__ CUtensorMap xmap, const TaskDev* __restrict__ tasks,
+            const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets, const float* __restrict__ U,
+            const double* __restrict__ yz, const double* __restrict__ z64, ResDev* __restrict__ res,
+            int64_t* __restrict__ band_out, int* err, float gamma, int nst)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ TcShared sh;
+
+    if (*(volatile const int*)err & ERR_TIMEOUT) return;   // another CTA already gave up
+    const TaskDev T = tasks[blockIdx.x];
+    const SlotDev& S = slots[T.slot];
+    const DsDev D = dsets[S.ds];
+    const int kp = D.kp, nchunk = kp / 64, d = D.d;
+    const int64_t n = D.n;
+    const int ntiles = (int)((n + BN - 1) / BN);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // 1024-byte aligned operand area: A planes (hi, lo) then STAGES x B planes (hi, lo)
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_plane = (uint32_t)nchunk * plane_bytes_rows(BM);      // bytes of one A plane
+    const uint32_t b_plane = (uint32_t)nchunk * plane_bytes_rows(BN);      // bytes of one B plane
+    uint8_t* Ahi = base;
+    uint8_t* Alo = base + a_plane;
+    uint8_t* Bst = base + 2 * a_plane;                                     // stage s at Bst + s * 2 * b_plane
+
+    // ---- A planes from the FP32 directions, with the folded -y_z columns ----------------
+    for (int e = threadIdx.x; e < BM * kp; e += NTHREADS) {
+        const int r = e / kp, k = e - r * kp;
+        float hi = 0.f, lo = 0.f;
+        if (r < T.nj) {
+            const int j = T.j0 + r;
+            if (k < d) {
+                const float u = U[S.uoff + (int64_t)j * S.ldx + k];
+                hi = bf16_val(bf16_bits(u));
+                lo = u - hi;   // exact in FP32
+            } else if (k == d || k == d + 1) {
+                const double y = yz[S.roff + j];
+                const float y1 = bf16_val(bf16_bits((float)y));
+                const double r1 = y - (double)y1;
+                const float y2 = bf16_val(bf16_bits((float)r1));
+                const double r2 = r1 - (double)y2;
+                const float y3 = bf16_val(bf16_bits((float)r2));
+                if (k == d) {
+                    hi = -y1;
+                    lo = -y2;
+                } else {
+                    hi = 0.f;
+                    lo = -y3;
+                }
+            }
+        }
+        const int c = k >> 6, kk = k & 63;
+        const uint32_t off = (uint32_t)c * plane_bytes_rows(BM) + sw128_offset(r, kk);
+        *reinterpret_cast<uint16_t*>(Ahi + off) = bf16_bits(hi);
+        *reinterpret_cast<uint16_t*>(Alo + off) = bf16_bits(lo);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&sh.full[s], 1);
+            mbar_init(&sh.empty[s], 1);
+        }
+        sh.mma_tiles = 0;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh.acc_full[b], 1);
+            mbar_init(&sh.acc_empty[b], 4);   // one arrival per epilogue warp
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh.tmem_base;
+
+    if (warp == 0) {
+        // ---- TMA producer ------------------------------------------------------------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % nst;
+                if (t >= nst && !mbar_wait(&sh.empty[s], ((t / nst) - 1) & 1, err)) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    sh.abort = 1;
+                    break;
+                }
+                if (*(volatile int*)&sh.abort) break;
+                uint8_t* st = Bst + (size_t)s * 2 * b_plane;
+                mbar_arrive_expect_tx(&sh.full[s], 2 * b_plane);
+                for (int p = 0; p < 2; ++p)
+                    for (int c = 0; c < nchunk; ++c)
+                        tma_load_2d(st + p * b_plane + c * plane_bytes_rows(BN), &xmap, p * kp + c * 64, t * BN,
+                                    &sh.full[s]);
+                issued = t + 1;
+            }
+            if (*(volatile int*)&sh.abort) {
+                // do not leave copies in flight into this CTA's shared memory: wait (bounded) for the
+                // loads the MMA issuer has not consumed
+                for (int t = *(volatile int*)&sh.mma_tiles; t < issued; ++t) mbar_wait(&sh.full[t % nst], (t / nst) & 1, err, false);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ---------------------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % nst, b = t & 1;
+                if (!mbar_wait(&sh.full[s], (t / nst) & 1, err) ||
+                    (t >= 2 && !mbar_wait(&sh.acc_empty[b], ((t >> 1) - 1) & 1, err))) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    sh.abort = 1;
+                    break;
+                }
+                if (*(volatile int*)&sh.abort) break;
+                tc_fence_after();
+                const uint32_t bst = smem_u32(Bst + (size_t)s * 2 * b_plane);
+                const uint32_t bhi = bst, blo = bst + b_plane;
+                const uint32_t dtm = tmem + (uint32_t)(b * BN);
+                uint32_t acc = 0;
+                // products (A plane, B plane): (hi, hi), (lo, hi), (hi, lo)
+                for (int pr = 0; pr < 3; ++pr) {
+                    const uint32_t ap = pr == 1 ? alo : ahi;
+                    const uint32_t bp = pr == 2 ? blo : bhi;
+                    for (int c = 0; c < nchunk; ++c) {
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = sw128_desc(ap + c * plane_bytes_rows(BM) + ks * 32);
+                            const uint64_t bd = sw128_desc(bp + c * plane_bytes_rows(BN) + ks * 32);
+                            umma_bf16(dtm, ad, bd, acc);
+                            acc = 1;
+                        }
+                    }
+                }
+                umma_commit(&sh.empty[s]);
+                umma_commit(&sh.acc_full[b]);
+                *(volatile int*)&sh.mma_tiles = t + 1;
+            }
+            const int done = *(volatile int*)&sh.mma_tiles;
+            if (*(volatile int*)&sh.abort && done > 0) {
+                // let the last issued MMAs finish before tensor memory is released
+                const int t = done - 1;
+                mbar_wait(&sh.acc_full[t & 1], (t >> 1) & 1, err, false);
+            }
+        }
+    } else {
+        // ---- epilogue: one direction per thread -------------------------------------------------
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;          // direction row = TMEM lane
+        const bool live = row < T.nj;
+        const int j = T.j0 + row;
+        const float gzn = gamma * S.znorm;
+        const float* ujs = U + S.uoff + (int64_t)(live ? j : T.j0) * S.ldx;
+        const double* zrow = z64 + S.zoff64;
+        int64_t lt = 0, gt = 0, nband = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            const int64_t col0 = (int64_t)t * BN;
+            if (!mbar_wait(&sh.acc_full[b], (t >> 1) & 1, err)) {
+                atomicOr(err, ERR_TIMEOUT);
+                sh.abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const int valid = (n - col0 < BN) ? (int)(n - col0) : BN;
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
+                // the chunk's 32 point norms, one per lane, broadcast per column below
+                const int cl = ch * 32 + lane;
+                const float xl = cl < valid ? D.xnorm[col0 + cl] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const int c = ch * 32 + k;
+                    const float xnk = __shfl_sync(0xFFFFFFFFu, xl, k);
+                    if (!live || c >= valid) continue;
+                    const float bnd = fmaf(gamma, xnk, gzn);
+                    const float tv = v[k];
+                    if (tv < -bnd) {
+                        lt++;
+                    } else if (tv > bnd) {
+                        gt++;
+                    } else {
+                        const int64_t i = col0 + c;
+                        int sgn;
+                        if (D.X64) sgn = rrsdev::exact_sign<double>(ujs, 1, D.X64 + i * d, zrow, d, err);
+                        else sgn = rrsdev::exact_sign<float>(ujs, 1, D.X32 + i * D.ldx, zrow, d, err);
+                        lt += (sgn < 0);
+                        gt += (sgn > 0);
+                        nband++;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.acc_empty[b]);
+        }
+        if (live) {
+            const int64_t le = n - gt, ge = n - lt;
+            const int64_t cmin = le < ge ? le : ge;
+            res[S.roff + j] = ResDev{(double)cmin / (double)n, cmin};
+        }
+        if (band_out) {
+            for (int o = 16; o >= 1; o >>= 1) nband += __shfl_xor_sync(0xFFFFFFFFu, nband, o);
+            if (lane == 0) atomicAdd((unsigned long long*)&band_out[T.slot], (unsigned long long)nband);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+}
+
+__global__ void k_build_planes(const float* __restrict__ X32, int64_t n, int d, int ldx, int kp,
+                               uint16_t* __restrict__ Xbf)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * kp) return;
+    const int64_t i = e / kp;
+    const int k = (int)(e - i * kp);
+    float hi = 0.f, lo = 0.f;
+    if (k < d) {
+        const float x = X32[i * ldx + k];
+        hi = bf16_val(bf16_bits(x));
+        lo = x - hi;
+    } else if (k == d || k == d + 1) {
+        hi = 1.0f;   // multiplies the folded -u'z parts of the direction planes
+    }
+    Xbf[i * 2 * kp + k] = bf16_bits(hi);
+    Xbf[i * 2 * kp + kp + k] = bf16_bits(lo);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+int tc_stages(int kp) { return kp <= 64 ? STAGES : 2; }
+
+size_t tc_smem_bytes(int kp)
+{
+    const size_t nchunk = (size_t)kp / 64;
+    return 1024 /* alignment slack */ + 2 * nchunk * plane_bytes_rows(BM) +
+           (size_t)tc_stages(kp) * 2 * nchunk * plane_bytes_rows(BN);
+}
+
+}  // namespace
+
+float band_gamma_tc(int kp)
+{
+    // split residuals 3 * 2^-16 |u||x| (with 1% slack), FP32 accumulation of 3*kp products at most one
+    // 2^-23 relative error each, the 2^-24 rounding of y_z's three BF16 parts; times 1.25
+    const double g = 3.03 * 0x1p-16 + 3.03 * (double)kp * 0x1p-23 + 0x1p-22;
+    return (float)(1.25 * g);
+}
+
+bool hd_tc_supported(int d) { return d >= 1 && d + 2 <= 128; }
+
+cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
+                                     cudaStream_t st)
+{
+    const int64_t total = n * kp;
+    const int nt = 256;
+    k_build_planes<<<(unsigned)((total + nt - 1) / nt), nt, 0, st>>>(X32, n, d, ldx, kp, Xbf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds_dev,
+                         const DsDev& ds_host, const float* U, const double* yz, const double* z64, ResDev* res,
+                         int64_t* band_out, int* err, cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int kp = ds_host.kp;
+    if (kp != 64 && kp != 128) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {(cuuint64_t)(2 * kp), (cuuint64_t)ds_host.n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(2 * kp) * sizeof(uint16_t)};
+    const cuuint32_t box[2] = {64, BN};
+    const cuuint32_t estride[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ds_host.Xbf, gdim, gstride, box, estride,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem_bytes(kp);
+    cudaError_t e = cudaFuncSetAttribute(k_hd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    k_hd_tc<<<ntasks, NTHREADS, smem, st>>>(map, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
+                                            band_gamma_tc(kp), tc_stages(kp));
+    return cudaGetLastError();
 }
 
 }  // namespace rrs

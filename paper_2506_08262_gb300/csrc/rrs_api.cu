@@ -334,7 +334,8 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             P.max_ldx = std::max(P.max_ldx, D.ldx);
             for (int j0 = 0; j0 < m; j0 += 128) P.gen_tasks.push_back(TaskDev{s, j0, std::min(128, m - j0), 0});
             if (R.kind == RRS_HALFSPACE) {
-                const int nt = (m + 63) / 64;
+                const int cap = precision == RRS_PREC_SPLIT_BF16X3 ? 128 : 64;   // directions per CTA
+                const int nt = (m + cap - 1) / cap;
                 const int per = (m + nt - 1) / nt;
                 for (int j0 = 0; j0 < m; j0 += per) P.hd_tasks.push_back(TaskDev{s, j0, std::min(per, m - j0), 0});
             } else {
@@ -424,8 +425,8 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
         if (P.n_hd[l] > 0) {
             if (P.precision == RRS_PREC_SPLIT_BF16X3) {
                 StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
-                CUDA_TRY(launch_hd_tc(P.d_hd, P.n_hd[l], P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res, nullptr,
-                                      ctx->d_err, st));
+                CUDA_TRY(launch_hd_tc(P.d_hd, P.n_hd[l], P.d_slots, P.d_ds, P.ds[0], P.U, P.yz, P.z64, P.res,
+                                      nullptr, ctx->d_err, st));
                 ctx->stage_launches[RRS_STAGE_HD_TC]++;
             } else {
                 StageTimer t(ctx, RRS_STAGE_HD_SIMT, st, capturing);
@@ -911,8 +912,8 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
         trace("debug_round_depths: y_z done");
         if (kind == RRS_HALFSPACE) {
             if (precision == RRS_PREC_SPLIT_BF16X3)
-                CUDA_TRY(launch_hd_tc(P.d_hd, (int)P.hd_tasks.size(), P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res,
-                                      band, ctx->d_err, st));
+                CUDA_TRY(launch_hd_tc(P.d_hd, (int)P.hd_tasks.size(), P.d_slots, P.d_ds, P.ds[0], P.U, P.yz, P.z64,
+                                      P.res, band, ctx->d_err, st));
             else
                 CUDA_TRY(launch_hd_simt(P.d_hd, (int)P.hd_tasks.size(), P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz,
                                         P.z64, P.res, band, ctx->d_err, st));

@@ -207,7 +207,7 @@ __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e
 // Renormalise the nonoverlapping expansion h[0..len) (increasing magnitude)
 // into a shorter nonadjacent one (Shewchuk 1997, "Compress"); returns the
 // new length.
-__device__ __noinline__ int expansion_compress(double* h, int len)
+static __device__ __noinline__ int expansion_compress(double* h, int len)
 {
     if (len <= 1) return len;
     // top-down pass: sweep from the largest component, keeping the partial

@@ -78,7 +78,7 @@ enum : int {
 // Near-tie band factors: a point is re-checked exactly when
 // |t| <= gamma * (|x| + |z|), t the fast projection difference.
 __host__ __device__ float band_gamma_fp32(int d);
-float band_gamma_tc(int d);
+float band_gamma_tc(int kp);
 
 // Set the text that rrs_last_error() returns on this thread (rrs_api.cu).
 void set_last_error(const char* msg);
@@ -117,8 +117,9 @@ int pdap_max_group(int n, int ldx, int m);
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
                                      cudaStream_t st);
-cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds,
-                         const float* U, const double* yz, const double* z64, ResDev* res,
+// tasks of up to 128 directions of slots that all use the dataset ds_host (host copy of ds_dev[0..])
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds_dev,
+                         const DsDev& ds_host, const float* U, const double* yz, const double* z64, ResDev* res,
                          int64_t* band_out, int* err, cudaStream_t st);
 bool hd_tc_supported(int d);
 

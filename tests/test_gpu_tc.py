@@ -1,0 +1,89 @@
+"""GPU parity of the tensor-core halfspace path (tcgen05, split-BF16x3 products).
+
+Halfspace counts are exact whatever the projection arithmetic, because every
+point in the near-tie band is re-checked with an exact sign test; so the
+tensor-core path must reproduce the CPU oracle bit for bit, and the FP32 path
+as well.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_08262_gb300 as rrs
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+H = 0
+TC = rrs.RRS_PREC_SPLIT_BF16X3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from __graft_entry__ import build
+    build()
+    c = rrs.Context(0)
+    yield c
+    c.close()
+
+
+def run(ctx, X, Z, k, r, alpha, seed, precision):
+    did = ctx.register(torch.from_numpy(X).cuda())
+    try:
+        dep, cnt, best, ch = ctx.depth(did, torch.from_numpy(Z).cuda(), H, k, r, alpha, seed, precision=precision,
+                                       rounds=True)
+        return {"depth": dep.cpu().numpy(), "count": cnt.cpu().numpy(), "best": best.cpu().numpy(),
+                "choice": ch.cpu().numpy()}
+    finally:
+        ctx.free(did)
+
+
+def test_tc_tiny_case_matches_oracle(ctx):
+    X, Z = workloads.gaussian_cloud(77, 300, 5, 2, dtype=np.float32)
+    g = run(ctx, X, Z, 20, 2, 0.5, 3, TC)
+    ref = oracle.rrs(X, Z, H, 20, 2, 0.5, 3)
+    np.testing.assert_array_equal(g["count"], ref["count"])
+    np.testing.assert_array_equal(g["best"], ref["best"])
+
+
+@pytest.mark.parametrize("n,d,dtype", [(1, 1, np.float32), (129, 2, np.float64), (1000, 10, np.float32),
+                                       (3001, 50, np.float32), (2500, 62, np.float32), (1537, 100, np.float32),
+                                       (777, 126, np.float64)])
+def test_tc_halfspace_bit_exact(ctx, n, d, dtype):
+    X, Z = workloads.gaussian_cloud(n * 7 + d, n, d, 5, dtype=dtype, zscale=1.3)
+    Z[0] = X[0]
+    g = run(ctx, X, Z, 300, 3, 0.7, 11, TC)
+    ref = oracle.rrs(X, Z, H, 300, 3, 0.7, 11)
+    np.testing.assert_array_equal(g["count"], ref["count"])
+    np.testing.assert_array_equal(g["depth"], ref["depth"])
+    np.testing.assert_array_equal(g["best"], ref["best"])
+
+
+def test_tc_equals_fp32_path_on_heavy_tails(ctx):
+    P = workloads.c3(n=4000, nq=12)
+    a = run(ctx, P.X, P.Z, 400, 4, P.alpha, 0, TC)
+    b = run(ctx, P.X, P.Z, 400, 4, P.alpha, 0, rrs.RRS_PREC_FP32_SIMT)
+    for key in ("count", "depth", "best", "choice"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+def test_tc_round_counts_exact_and_band_sound(ctx):
+    # per-direction counts for caller-supplied directions against the oracle, plus the
+    # number of near-tie re-checks (every point whose fast sign could be wrong is in the band)
+    P = workloads.c3(n=2049, nq=3)
+    m = 128
+    U = np.stack([oracle.directions(5, q, 0, m, P.d, 0.9) for q in range(3)])
+    did = ctx.register(torch.from_numpy(P.X).cuda())
+    dep = torch.empty((3, m), dtype=torch.float64, device="cuda")
+    cnt = torch.empty((3, m), dtype=torch.int64, device="cuda")
+    band = torch.zeros(3, dtype=torch.int64, device="cuda")
+    rrs.rrs_debug_round_depths(ctx.handle, did, torch.from_numpy(P.Z).cuda(), 3, rrs.RRS_F32, H, m,
+                               torch.from_numpy(U).cuda(), TC, dep, cnt, band)
+    ctx.free(did)
+    c = cnt.cpu().numpy()
+    for q in range(3):
+        for j in range(0, m, 7):
+            assert c[q, j] == oracle.univariate(H, P.X, P.Z[q], U[q, j])[1]
+    # band re-checks are a small fraction of all point-direction pairs
+    assert int(band.sum()) < 0.02 * 3 * m * P.n
