@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--nq", type=int, default=1000, help="queries per kind (default: the full workload)")
+    ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
+    ap.add_argument("--workload", choices=["c2", "c3"], default="c2",
+                    help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths")
     return ap.parse_args()
 
 
@@ -206,7 +208,7 @@ def run_ours(args):
 
     kinds = (workloads.PROJECTION, workloads.ASYM_PROJECTION)
     P2 = workloads.c2()
-    X, Z = P2.X, P2.Z[:args.nq]
+    X, Z = P2.X, P2.Z[:args.nq or P2.nq]
     nq, n, d = Z.shape[0], X.shape[0], X.shape[1]
     k, r, alpha, seed = P2.k, P2.r, P2.alpha, P2.seed
     m = -(-k // r)
@@ -337,10 +339,105 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+WORKLOAD_C3 = ("halfspace depth, d=50, n=100000 Student-t(3) rows mapped by a random SPD square root, "
+               "10000 queries from the same law, k=2000 dirs over r=20 rounds, alpha=0.9, FP32 data")
+
+
+def run_c3(args):
+    """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    P = workloads.c3(nq=args.nq or 10_000)
+    n, d, nq, k, r = P.n, P.d, P.nq, P.k, P.r
+    m = -(-k // r)
+    ctx = rrs.rrs_create(0, 0)
+    did = rrs.rrs_register_dataset(ctx, torch.from_numpy(P.X).to(dev), n, d, rrs.RRS_F32, True)
+    Zd = torch.from_numpy(P.Z).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    out = {}
+    results = {}
+    for name, prec in (("tc", rrs.RRS_PREC_SPLIT_BF16X3), ("fp32", rrs.RRS_PREC_FP32_SIMT)):
+        dep = torch.empty(nq, dtype=torch.float64, device=dev)
+        cnt = torch.empty(nq, dtype=torch.int64, device=dev)
+
+        def step():
+            rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F32, True, rrs.RRS_HALFSPACE, k, r, P.alpha, P.seed, prec,
+                          dep, cnt, None, None, True, stream)
+        for _ in range(max(3, args.warmup)):
+            step()
+        rrs.rrs_check(ctx, stream)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        rrs.rrs_profile_enable(ctx, True)
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        prof = rrs.rrs_profile_read(ctx)
+        rrs.rrs_profile_enable(ctx, False)
+        clocks = sampler.stop()
+        rrs.rrs_check(ctx, stream)
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        stage = "hd_tc" if prec == rrs.RRS_PREC_SPLIT_BF16X3 else "hd_simt"
+        kms, kl = prof[stage]
+        elems_per_launch = nq * m * n
+        avg_ms = kms / max(1, kl)
+        entry = {"ms_per_step": ms, "value": nq / (ms / 1000), "unit": "query-depths/s",
+                 "pd_per_s": nq * r * m * n / (ms / 1000), "kernel_ms_per_launch": avg_ms,
+                 "kernel_share": kms / max(1e-9, sum(v[0] for v in prof.values())), "clocks": clocks}
+        if name == "tc":
+            flops = 6.0 * d * elems_per_launch   # three BF16 products of d terms per point-direction pair
+            achieved = flops / (avg_ms / 1000) / 1e12
+            entry["roofline"] = {"bound": "tensor", "kernel": "k_hd_tc", "achieved": achieved, "peak": bf16_peak,
+                                 "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                                 "flops_per_launch": flops}
+        else:
+            flops = 2.0 * d * elems_per_launch
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+            achieved = flops / (avg_ms / 1000) / 1e12
+            entry["roofline"] = {"bound": "alu", "kernel": "k_hd_simt", "achieved": achieved, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                                 "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x 2070 MHz"}
+        results[name] = (dep.cpu().numpy(), cnt.cpu().numpy())
+        out[name] = entry
+    assert np.array_equal(results["tc"][1], results["fp32"][1]), "tensor-core and FP32 counts differ"
+    line = {"metric": METRIC, "value": out["tc"]["value"], "unit": "query-depths/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": out["tc"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_C3, "n": n, "d": d, "queries": nq, "k": k, "r": r,
+                       "l2": "flushed between timed steps (512 MiB device write)"},
+            "tensor_core": out["tc"], "fp32_cuda_core": out["fp32"],
+            "speedup_tc_over_fp32": out["fp32"]["ms_per_step"] / out["tc"]["ms_per_step"],
+            "counts_identical": True}
+    rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_c3(args)
     else:
         run_ours(args)
 

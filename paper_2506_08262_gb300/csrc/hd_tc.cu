@@ -10,10 +10,14 @@
 // bound on the error of t, and re-checks every |t| <= b with the exact FP64
 // sign test, so the counts are exact.
 //
-// CTA layout (192 threads): warp 0 streams point tiles with TMA into a
-// 4-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-5 read
-// the accumulator (one direction per TMEM lane) and count.  The accumulator is
-// double buffered so the epilogue of tile t overlaps the MMAs of tile t+1.
+// CTA layout (320 threads): warp 0 streams point tiles with TMA into a
+// 4-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-9 read
+// the accumulator (one direction per TMEM lane, two warps per lane quarter,
+// each taking half of a tile's columns) and count.  The accumulator is double
+// buffered so the epilogue of tile t overlaps the MMAs of tile t+1.  Per
+// 32-column chunk the epilogue first takes min|t| and the sign-bit count; only
+// a chunk whose min|t| reaches the chunk's largest band goes through the
+// per-point band test.
 // Every wait on an mbarrier is bounded; on timeout the CTA flags ERR_TIMEOUT
 // and winds down.
 #include <cuda.h>
@@ -33,7 +37,8 @@ namespace {
 constexpr int BM = 128;          // directions per CTA (TMEM lanes)
 constexpr int BN = 128;          // points per tile (accumulator columns)
 constexpr int STAGES = 4;
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 8;                      // epilogue warps: two per TMEM lane quarter
+constexpr int NTHREADS = 64 + 32 * NEPI;
 
 __host__ __device__ constexpr int plane_bytes_rows(int rows) { return rows * 128; }   // one 64-wide K chunk
 
@@ -160,6 +165,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ TcShared sh;
+    __shared__ float xnW[NEPI][32];
+    __shared__ long long partial_lt[NEPI][32], partial_gt[NEPI][32];
 
     if (*(volatile const int*)err & ERR_TIMEOUT) return;   // another CTA already gave up
     const TaskDev T = tasks[blockIdx.x];
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         sh.mma_tiles = 0;
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh.acc_full[b], 1);
-            mbar_init(&sh.acc_empty[b], 4);   // one arrival per epilogue warp
+            mbar_init(&sh.acc_empty[b], NEPI);   // one arrival per epilogue warp
         }
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,7 +313,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ---- epilogue: one direction per thread -------------------------------------------------
+        const int e = warp - 2;                 // 0..NEPI-1
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = e >> 2;                // which half of the tile's columns
         const int row = q * 32 + lane;          // direction row = TMEM lane
         const bool live = row < T.nj;
         const int j = T.j0 + row;
@@ -317,25 +326,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1;
             const int64_t col0 = (int64_t)t * BN;
-            if (!mbar_wait(&sh.acc_full[b], (t >> 1) & 1, err)) {
-                atomicOr(err, ERR_TIMEOUT);
-                sh.abort = 1;
+            // one lane waits, the whole warp follows its verdict (tcgen05.ld needs the full warp)
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&sh.acc_full[b], (t >> 1) & 1, err) ? 1 : 0;
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            __syncwarp();
+            if (!ok) {
+                if (lane == 0) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    sh.abort = 1;
+                }
                 break;
             }
             tc_fence_after();
             const int valid = (n - col0 < BN) ? (int)(n - col0) : BN;
-            for (int ch = 0; ch < BN / 32; ++ch) {
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 64; ++cc) {
+                const int ch = half * (BN / 64) + cc;
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
-                // the chunk's 32 point norms, one per lane, broadcast per column below
                 const int cl = ch * 32 + lane;
                 const float xl = cl < valid ? D.xnorm[col0 + cl] : 0.0f;
+                float xmax = xl;
 #pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xFFFFFFFFu, xmax, o));
+                __syncwarp();
+                xnW[e][lane] = xl;
+                __syncwarp();
+                if (!live) continue;
+                const bool full = ch * 32 + 32 <= valid;
+                if (full) {
+                    float mn = fabsf(v[0]);
+                    uint32_t neg = __float_as_uint(v[0]) >> 31;
+#pragma unroll
+                    for (int k = 1; k < 32; ++k) {
+                        mn = fminf(mn, fabsf(v[k]));
+                        neg += __float_as_uint(v[k]) >> 31;
+                    }
+                    if (mn > fmaf(gamma, xmax, gzn)) {   // no point of the chunk is near a tie
+                        lt += neg;
+                        gt += 32 - neg;
+                        continue;
+                    }
+                }
                 for (int k = 0; k < 32; ++k) {
                     const int c = ch * 32 + k;
-                    const float xnk = __shfl_sync(0xFFFFFFFFu, xl, k);
-                    if (!live || c >= valid) continue;
-                    const float bnd = fmaf(gamma, xnk, gzn);
+                    if (c >= valid) break;
+                    const float bnd = fmaf(gamma, xnW[e][k], gzn);
                     const float tv = v[k];
                     if (tv < -bnd) {
                         lt++;
@@ -356,11 +393,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.acc_empty[b]);
         }
-        if (live) {
-            const int64_t le = n - gt, ge = n - lt;
-            const int64_t cmin = le < ge ? le : ge;
-            res[S.roff + j] = ResDev{(double)cmin / (double)n, cmin};
-        }
+        // the two warps of a lane quarter each counted half of the columns
+        partial_lt[e][lane] = lt;
+        partial_gt[e][lane] = gt;
         if (band_out) {
             for (int o = 16; o >= 1; o >>= 1) nband += __shfl_xor_sync(0xFFFFFFFFu, nband, o);
             if (lane == 0) atomicAdd((unsigned long long*)&band_out[T.slot], (unsigned long long)nband);
@@ -368,6 +403,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (warp >= 2 && warp < 6) {
+        const int e = warp - 2;   // warps e and e + 4 read the same TMEM lanes
+        const int row = (warp & 3) * 32 + lane;
+        if (row < T.nj && !sh.abort) {
+            const long long l2 = partial_lt[e][lane] + partial_lt[e + 4][lane];
+            const long long g2 = partial_gt[e][lane] + partial_gt[e + 4][lane];
+            const int64_t le = n - g2, ge = n - l2;
+            const int64_t cmin = le < ge ? le : ge;
+            res[S.roff + T.j0 + row] = ResDev{(double)cmin / (double)n, cmin};
+        }
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
