@@ -322,6 +322,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const float gzn = gamma * S.znorm;
         const float* ujs = U + S.uoff + (int64_t)(live ? j : T.j0) * S.ldx;
         const double* zrow = z64 + S.zoff64;
+        const float yz32 = (float)yz[S.roff + (live ? j : T.j0)];
+        const float g32 = band_gamma_fp32(d);
         int64_t lt = 0, gt = 0, nband = 0;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1;
@@ -379,10 +381,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     } else if (tv > bnd) {
                         gt++;
                     } else {
+                        // second stage: FP32 projection with its own, ~30x narrower, bound;
+                        // only what stays inside goes to the exact FP64 test
                         const int64_t i = col0 + c;
+                        const float* xr = D.X32 + i * D.ldx;
+                        float t32 = 0.0f;
+                        for (int l = 0; l < d; ++l) t32 = fmaf(ujs[l], xr[l], t32);
+                        t32 = t32 - yz32;
+                        const float b32 = g32 * (xnW[e][k] + S.znorm);
                         int sgn;
-                        if (D.X64) sgn = rrsdev::exact_sign<double>(ujs, 1, D.X64 + i * d, zrow, d, err);
-                        else sgn = rrsdev::exact_sign<float>(ujs, 1, D.X32 + i * D.ldx, zrow, d, err);
+                        if (t32 > b32) sgn = 1;
+                        else if (t32 < -b32) sgn = -1;
+                        else if (D.X64) sgn = rrsdev::exact_sign<double>(ujs, 1, D.X64 + i * d, zrow, d, err);
+                        else sgn = rrsdev::exact_sign<float>(ujs, 1, xr, zrow, d, err);
                         lt += (sgn < 0);
                         gt += (sgn > 0);
                         nband++;

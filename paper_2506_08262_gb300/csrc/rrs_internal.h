@@ -77,7 +77,9 @@ enum : int {
 
 // Near-tie band factors: a point is re-checked exactly when
 // |t| <= gamma * (|x| + |z|), t the fast projection difference.
-__host__ __device__ float band_gamma_fp32(int d);
+// FP32 path: |fl32 dot - exact| <= gamma_d sum|u x| (gamma_d ~ d 2^-24), plus one rounding of x to FP32
+// (FP64 inputs), of y_z to FP32 and of the final difference; twice that sum for slack.
+__host__ __device__ inline float band_gamma_fp32(int d) { return (float)((double)(d + 4) * 0x1p-23); }
 float band_gamma_tc(int kp);
 
 // Set the text that rrs_last_error() returns on this thread (rrs_api.cu).

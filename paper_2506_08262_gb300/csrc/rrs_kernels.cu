@@ -14,12 +14,6 @@ namespace rrs {
 
 using namespace rrsdev;
 
-__host__ __device__ float band_gamma_fp32(int d)
-{
-    // |fl32 dot - exact| <= gamma_d sum|u x| (gamma_d ~ d 2^-24), plus one rounding of x to FP32
-    // (FP64 inputs), of y_z to FP32 and of the final difference; twice that sum for slack.
-    return (float)((double)(d + 4) * 0x1p-23);
-}
 
 // ---------------------------------------------------------------------------
 // dataset and query preparation
