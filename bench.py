@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3"], default="c2",
-                    help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default="c2",
+                    help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
+                         "c4: 256 datasets batched in one graph-captured launch sequence")
+    ap.add_argument("--scale", type=float, default=1.0, help="c4: shrink n and query counts (tests)")
     return ap.parse_args()
 
 
@@ -432,12 +434,94 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD_C4 = ("batched: 256 datasets, n log-uniform [500, 50000], d uniform {5..100}, N(mu_k, Sigma_k), "
+               "1..1000 queries each, kind uniform over halfspace/projection/asymmetric, k=1000 over r=10, "
+               "alpha=0.9, FP32")
+
+
+def run_c4(args):
+    """All requests of the batched workload in one graph-captured launch sequence, against the same
+    requests issued one rrs_depth call at a time."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    problems = workloads.c4(scale=args.scale)
+    ctx = rrs.rrs_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    reqs, keep = [], []
+    total_q = 0
+    pd_total = 0
+    for i, P in enumerate(problems):
+        did = rrs.rrs_register_dataset(ctx, torch.from_numpy(P.X).to(dev), P.n, P.d, rrs.RRS_F32, True)
+        Z = torch.from_numpy(P.Z).to(dev)
+        out = torch.empty(P.nq, dtype=torch.float64, device=dev)
+        keep.append((did, Z, out, P))
+        reqs.append(rrs.rrs_request(dataset_id=did, Z=Z.data_ptr(), n_queries=P.nq, dtype=rrs.RRS_F32,
+                                    kind=P.kind, n_dirs=P.k, n_refinements=P.r, cap_shrink=P.alpha, seed=P.seed,
+                                    depth_out=out.data_ptr()))
+        total_q += P.nq
+        pd_total += P.nq * P.r * (-(-P.k // P.r)) * P.n
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps):
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    def batched():
+        rrs.rrs_depth_batched(ctx, reqs, use_graph=True, stream=stream)
+
+    def one_by_one():
+        for did, Z, out, P in keep:
+            rrs.rrs_depth(ctx, did, Z, P.nq, rrs.RRS_F32, True, P.kind, P.k, P.r, P.alpha, P.seed,
+                          rrs.RRS_PREC_FP32_SIMT, out, None, None, None, True, stream)
+
+    for _ in range(max(3, args.warmup)):
+        batched()
+    rrs.rrs_check(ctx, stream)
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = rrs.rrs_launch_count(ctx)
+    ms_b = timed(batched, args.steps)
+    launches = rrs.rrs_launch_count(ctx) - launches0
+    clocks = sampler.stop()
+    res_b = [out.cpu().numpy().copy() for _, _, out, _ in keep]
+    one_by_one()
+    torch.cuda.synchronize()
+    ms_s = timed(one_by_one, max(1, args.steps // 2))
+    rrs.rrs_check(ctx, stream)
+    same = all(np.array_equal(res_b[i], keep[i][2].cpu().numpy()) for i in range(len(keep)))
+    line = {"metric": METRIC, "value": total_q / (ms_b / 1000), "unit": "query-depths/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_C4, "datasets": len(problems), "queries": total_q, "scale": args.scale,
+                       "l2": "flushed between timed steps (512 MiB device write)"},
+            "pd_per_s": pd_total / (ms_b / 1000), "gpu_launches": int(launches),
+            "one_call_per_request": {"ms_per_step": ms_s, "value": total_q / (ms_s / 1000)},
+            "speedup_batched_over_per_request": ms_s / ms_b, "results_identical": bool(same), "clocks": clocks}
+    for did, _, _, _ in keep:
+        rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "c3":
         run_c3(args)
+    elif args.workload == "c4":
+        run_c4(args)
     else:
         run_ours(args)
 
