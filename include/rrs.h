@@ -226,6 +226,58 @@ rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on);
 rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out);
 
 /*
+ * Serving (continuous batching).  A server keeps a fixed pool of query slots
+ * on the device.  Requests queue in arrival order; each rrs_server_step admits
+ * the waiting requests that fit in the free slots, runs ONE refinement round
+ * (Alg. 4: generate, project + univariate depth, minimum and pole update) for
+ * every active query in shared launches -- each query at its own round -- and
+ * retires the requests whose last round just ran by copying their depths to the
+ * caller's host buffer.  Requests that arrive while others are on the GPU thus
+ * join the next step's launches.  Every query keeps its own direction stream
+ * (counter q = its row in its request) and state, so a request's depths do not
+ * depend on what else is being served: they equal rrs_depth's FP32 results on
+ * that request alone.
+ */
+typedef struct rrs_server rrs_server;
+
+/*
+ * rrs_server_create - a server on ctx with max_slots query slots, each able to
+ * hold a request of up to max_dirs_per_round directions per round (m) and
+ * dimension max_d.  Device memory for the pool is taken once (counted against
+ * the context's budget).  stream: cudaStream_t every server operation is
+ * ordered on (NULL = legacy default stream).  Errors: INVALID_ARG, BUDGET, CUDA.
+ */
+rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_per_round, int32_t max_d,
+                             void* stream, rrs_server** out);
+
+/*
+ * rrs_server_submit - queue a request: queries Z (host, n_queries x d, dtype)
+ * against a registered dataset with the RRS parameters of rrs_depth (FP32
+ * arithmetic).  Z and depth_out (host, n_queries doubles) must stay valid until
+ * rrs_server_poll reports the request done; the dataset must stay registered.
+ * *request_id_out receives the request's id.  Errors: INVALID_ARG, NOT_FOUND,
+ * UNSUPPORTED (request larger than the slot shape or pool).
+ */
+rrs_status rrs_server_submit(rrs_server* server, int64_t dataset_id, const void* Z, int64_t n_queries,
+                             int32_t dtype, int32_t kind, int32_t n_dirs, int32_t n_refinements,
+                             double cap_shrink, uint64_t seed, double* depth_out, int64_t* request_id_out);
+
+/*
+ * rrs_server_step - admit what fits, run one round for all active queries,
+ * retire finished requests (their host copies are enqueued on the stream).
+ * Returns after enqueueing.  *active_queries_out / *pending_requests_out
+ * (optional) receive the queries in flight and the requests still waiting.
+ */
+rrs_status rrs_server_step(rrs_server* server, int32_t* active_queries_out, int32_t* pending_requests_out);
+
+/* rrs_server_poll - *done_out = 1 once the request's depths are in its host
+ * buffer (the request is then forgotten), else 0.  Errors: NOT_FOUND, CUDA. */
+rrs_status rrs_server_poll(rrs_server* server, int64_t request_id, int32_t* done_out);
+
+/* rrs_server_destroy - wait for the stream, drop queued requests, free the pool. */
+rrs_status rrs_server_destroy(rrs_server* server);
+
+/*
  * rrs_depth_noalloc - rrs_depth for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a deployment variant.
  *

@@ -87,6 +87,14 @@ _SIGS = {
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "rrs_profile_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_create": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                           ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_submit": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
+                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_poll": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_destroy": ([ctypes.c_void_p], ctypes.c_int32),
     "rrs_depth_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
@@ -207,6 +215,39 @@ def rrs_depth_noalloc(X, n: int, d: int, dtype: int, Z, n_queries: int, kind: in
     _check(load().rrs_depth_noalloc(_ptr(X), n, d, dtype, _ptr(Z), n_queries, kind, n_dirs, n_refinements,
                                     float(cap_shrink), seed, _ptr(depth_out), _ptr(count_out), _stream(stream)),
            "rrs_depth_noalloc")
+
+
+def rrs_server_create(ctx: int, max_slots: int, max_dirs_per_round: int, max_d: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().rrs_server_create(ctx, max_slots, max_dirs_per_round, max_d, _stream(stream), ctypes.byref(h)),
+           "rrs_server_create")
+    return h.value
+
+
+def rrs_server_submit(server: int, dataset_id: int, Z, n_queries: int, dtype: int, kind: int, n_dirs: int,
+                      n_refinements: int, cap_shrink: float, seed: int, depth_out) -> int:
+    rid = ctypes.c_int64()
+    _check(load().rrs_server_submit(server, dataset_id, _ptr(Z), n_queries, dtype, kind, n_dirs, n_refinements,
+                                    float(cap_shrink), seed, _ptr(depth_out), ctypes.byref(rid)),
+           "rrs_server_submit")
+    return rid.value
+
+
+def rrs_server_step(server: int):
+    """Returns (active queries, pending requests)."""
+    a, p = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().rrs_server_step(server, ctypes.byref(a), ctypes.byref(p)), "rrs_server_step")
+    return a.value, p.value
+
+
+def rrs_server_poll(server: int, request_id: int) -> bool:
+    done = ctypes.c_int32()
+    _check(load().rrs_server_poll(server, request_id, ctypes.byref(done)), "rrs_server_poll")
+    return bool(done.value)
+
+
+def rrs_server_destroy(server: int) -> None:
+    _check(load().rrs_server_destroy(server), "rrs_server_destroy")
 
 
 def rrs_check(ctx: int, stream=None) -> None:

@@ -50,6 +50,8 @@ struct SlotDev {
     int64_t cmin;
     int32_t best;
     float znorm;
+    int32_t round;         // next round (0-based) when launched in per-slot round mode
+    int32_t pad2;
 };
 
 // A block of directions of one slot handled by one CTA.
@@ -104,6 +106,12 @@ cudaError_t launch_yz_only(const TaskDev* tasks, int ntasks, const SlotDev* slot
                            const float* U, double* yz, cudaStream_t st);
 cudaError_t launch_scatter_dirs(const SlotDev* slots, int nslots, int m, int d, const float* Uin, float* U,
                                 cudaStream_t st);
+// Per-slot round mode (serving): each slot runs its own next round S.round; poles0 holds the
+// pole of slots at even rounds, poles1 of odd ones; argmin advances S.round.
+cudaError_t launch_gen_slotround(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles0,
+                                 const float* poles1, const double* z64, float* U, double* yz, cudaStream_t st);
+cudaError_t launch_argmin_slotround(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
+                                   const ResDev* res, float* poles0, float* poles1, cudaStream_t st);
 cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, float alpha, const float* pole,
                               float* U, cudaStream_t st);
 cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, int ldx, float* X32,

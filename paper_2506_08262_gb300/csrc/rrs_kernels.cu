@@ -177,17 +177,20 @@ cudaError_t launch_prep(const SlotDev* slots, int nslots, const DsDev* ds, float
 // ---------------------------------------------------------------------------
 
 __global__ void k_gen(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
-                      const float* __restrict__ poles, const double* __restrict__ z64, float* __restrict__ U,
-                      double* __restrict__ yz, int round0)
+                      const float* __restrict__ poles, const float* __restrict__ poles1,
+                      const double* __restrict__ z64, float* __restrict__ U, double* __restrict__ yz, int round0)
 {
     const TaskDev T = tasks[blockIdx.x];
     const int jl = threadIdx.x;
     if (jl >= T.nj) return;
     const SlotDev& S = slots[T.slot];
+    // launch-wide round, or (round0 < 0) the slot's own round with its pole buffer by parity
+    const int rnd = round0 >= 0 ? round0 : S.round;
+    const float* pcur = round0 >= 0 ? poles : ((rnd & 1) ? poles1 : poles);
     const int j = T.j0 + jl;
     float* u = U + S.uoff + (int64_t)j * S.ldx;
-    const float ap = alpha_power(S.alpha, round0);
-    stream_direction(S.seed, (uint32_t)S.qctr, (uint32_t)round0, (uint32_t)j, S.d, ap, poles + S.zoff32, u, 1);
+    const float ap = alpha_power(S.alpha, rnd);
+    stream_direction(S.seed, (uint32_t)S.qctr, (uint32_t)rnd, (uint32_t)j, S.d, ap, pcur + S.zoff32, u, 1);
     for (int l = S.d; l < S.ldx; ++l) u[l] = 0.0f;
     double acc = 0.0;
     const double* z = z64 + S.zoff64;
@@ -199,7 +202,15 @@ cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, c
                        const double* z64, float* U, double* yz, int round0, cudaStream_t st)
 {
     if (ntasks <= 0) return cudaSuccess;
-    k_gen<<<ntasks, 128, 0, st>>>(tasks, slots, poles_cur, z64, U, yz, round0);
+    k_gen<<<ntasks, 128, 0, st>>>(tasks, slots, poles_cur, nullptr, z64, U, yz, round0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_slotround(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles0,
+                                 const float* poles1, const double* z64, float* U, double* yz, cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    k_gen<<<ntasks, 128, 0, st>>>(tasks, slots, poles0, poles1, z64, U, yz, -1);
     return cudaGetLastError();
 }
 
@@ -413,13 +424,17 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
 // ---------------------------------------------------------------------------
 
 __global__ void k_argmin(SlotDev* __restrict__ slots, const int32_t* __restrict__ slot_list, int nlist,
-                         const float* __restrict__ U, const ResDev* __restrict__ res, const float* __restrict__ poles_cur,
-                         float* __restrict__ poles_next, int round0)
+                         const float* __restrict__ U, const ResDev* __restrict__ res, float* __restrict__ pa,
+                         float* __restrict__ pb, int round_arg)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nlist) return;
     SlotDev& S = slots[slot_list[w]];
+    // launch-wide round (pa = current poles, pb = next), or the slot's own round (pa even, pb odd)
+    const int round0 = round_arg >= 0 ? round_arg : S.round;
+    const float* poles_cur = round_arg >= 0 ? pa : ((round0 & 1) ? pb : pa);
+    float* poles_next = round_arg >= 0 ? pb : ((round0 & 1) ? pa : pb);
     const bool hd = (S.kind == 0);
     // lowest (value, index) over the m directions
     double bv = INFINITY;
@@ -461,6 +476,7 @@ __global__ void k_argmin(SlotDev* __restrict__ slots, const int32_t* __restrict_
             if (S.count_out) S.count_out[0] = hd ? S.cmin : -1;
             if (S.best_out) S.best_out[0] = S.best;
         }
+        if (round_arg < 0) S.round = round0 + 1;
     }
 }
 
@@ -471,7 +487,17 @@ cudaError_t launch_argmin(SlotDev* slots, const int32_t* slot_list, int nlist, c
     const int nt = 256;
     const int nb = (nlist * 32 + nt - 1) / nt;
     (void)last_round;
-    k_argmin<<<nb, nt, 0, st>>>(slots, slot_list, nlist, U, res, poles_cur, poles_next, round0);
+    k_argmin<<<nb, nt, 0, st>>>(slots, slot_list, nlist, U, res, const_cast<float*>(poles_cur), poles_next, round0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_argmin_slotround(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
+                                   const ResDev* res, float* poles0, float* poles1, cudaStream_t st)
+{
+    if (nlist <= 0) return cudaSuccess;
+    const int nt = 256;
+    const int nb = (nlist * 32 + nt - 1) / nt;
+    k_argmin<<<nb, nt, 0, st>>>(slots, slot_list, nlist, U, res, poles0, poles1, -1);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,468 @@
+// Serving loop: continuous (iteration-level) batching of RRS depth requests.
+//
+// A server owns a fixed pool of query slots on the device.  Requests wait in a
+// FIFO until enough slots are free; every rrs_server_step admits what fits,
+// then runs ONE refinement round (Alg. 4: generate, project + univariate depth,
+// minimum and pole update) for every active slot in shared launches -- each
+// slot at its own round -- and retires the requests whose last round just ran,
+// copying their depths to the caller's host buffer.  A request therefore joins
+// the GPU work of requests already in flight at the next step, and its
+// results do not depend on what else is in the mix: every query keeps its own
+// direction stream (counter index = row within its request) and state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "../../include/rrs.h"
+#include "rrs_ctx.h"
+#include "rrs_internal.h"
+
+using namespace rrs;
+
+namespace {
+
+rrs_status sfail(rrs_status st, const char* fmt, ...)
+{
+    char msg[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    set_last_error(msg);
+    return st;
+}
+
+#define S_TRY(expr)                                                                                  \
+    do {                                                                                             \
+        cudaError_t _e = (expr);                                                                     \
+        if (_e != cudaSuccess) {                                                                     \
+            cudaGetLastError();                                                                      \
+            return sfail(RRS_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e));                     \
+        }                                                                                            \
+    } while (0)
+
+struct Request {
+    int64_t id;
+    int64_t dataset;
+    const void* Zhost;
+    int64_t nq;
+    int32_t dtype, kind, k, r, m;
+    float alpha;
+    uint64_t seed;
+    double* out_host;
+    // device side once admitted
+    void* zdev = nullptr;
+    double* ddev = nullptr;
+    std::vector<int32_t> slots;
+    int rounds_done = 0;
+    cudaEvent_t done = nullptr;
+    bool finished = false;
+};
+
+// Admit kernel: place the new slots' descriptors and prepare their state.
+__global__ void k_admit(const SlotDev* __restrict__ src, const int32_t* __restrict__ idx, int cnt,
+                        SlotDev* __restrict__ slots, const DsDev* __restrict__ ds, float* __restrict__ z32,
+                        double* __restrict__ z64, float* __restrict__ poles0)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    SlotDev S = src[t];
+    const int d = S.d, ldx = S.ldx;
+    double acc = 0.0;
+    for (int l = 0; l < ldx; ++l) {
+        double v = 0.0;
+        if (l < d) {
+            v = S.zdtype == 0 ? (double)((const float*)S.zsrc)[l] : ((const double*)S.zsrc)[l];
+            z64[S.zoff64 + l] = v;
+            acc = __fma_rn(v, v, acc);
+        }
+        z32[S.zoff32 + l] = (float)v;
+        poles0[S.zoff32 + l] = (l == 0) ? 1.0f : 0.0f;
+    }
+    S.znorm = __double2float_ru(__dsqrt_ru(acc) * (1.0 + 1e-12));
+    S.dmin = 1.0;
+    S.cmin = ds[S.ds].n;
+    S.best = -1;
+    S.round = 0;
+    slots[idx[t]] = S;
+}
+
+}  // namespace
+
+struct rrs_server {
+    rrs_ctx* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    int cap = 0, max_m = 0, max_d = 0, max_ldx = 0;
+    // device arena
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    SlotDev* d_slots = nullptr;
+    float *d_z32 = nullptr, *d_p0 = nullptr, *d_p1 = nullptr, *d_U = nullptr;
+    double *d_z64 = nullptr, *d_yz = nullptr;
+    ResDev* d_res = nullptr;
+    DsDev* d_ds = nullptr;
+    int ds_cap = 0;
+    char* d_tab = nullptr;      // per-step tables (tasks, lists, new slots)
+    size_t tab_bytes = 0;
+    // host
+    std::vector<int32_t> free_slots;
+    std::deque<Request*> pending;
+    std::map<int64_t, Request*> requests;
+    std::vector<Request*> active;
+    std::map<int64_t, int> ds_index;   // dataset id -> row of d_ds
+    std::vector<DsDev> ds_host;
+    int64_t next_id = 1;
+    int active_queries = 0;
+};
+
+namespace {
+
+int padded(int d)
+{
+    int l = (d + 3) & ~3;
+    if (((l / 4) & 1) == 0) l += 4;
+    return l;
+}
+
+rrs_status ensure_dataset(rrs_server* S, int64_t id, int* row)
+{
+    auto f = S->ds_index.find(id);
+    if (f != S->ds_index.end()) {
+        *row = f->second;
+        return RRS_OK;
+    }
+    auto it = S->ctx->datasets.find(id);
+    if (it == S->ctx->datasets.end()) return sfail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)id);
+    if ((int)S->ds_host.size() >= S->ds_cap) return sfail(RRS_ERR_BUDGET, "server dataset table full");
+    const Dataset& D = it->second;
+    DsDev dd{};
+    dd.X32 = D.X32;
+    dd.X64 = D.X64;
+    dd.xnorm = D.xnorm;
+    dd.Xbf = D.Xbf;
+    dd.n = D.n;
+    dd.d = D.d;
+    dd.ldx = D.ldx;
+    dd.kp = D.kp;
+    dd.center = D.center;
+    dd.cov = D.cov;
+    dd.rc = D.rc;
+    const int r = (int)S->ds_host.size();
+    S->ds_host.push_back(dd);
+    S_TRY(cudaMemcpyAsync(S->d_ds + r, &S->ds_host[r], sizeof(DsDev), cudaMemcpyHostToDevice, S->st));
+    S->ds_index[id] = r;
+    *row = r;
+    return RRS_OK;
+}
+
+// Carve one per-step table area, growing it (stream-ordered) when needed.
+rrs_status step_table(rrs_server* S, size_t bytes)
+{
+    if (bytes <= S->tab_bytes) return RRS_OK;
+    if (S->d_tab) S_TRY(cudaFreeAsync(S->d_tab, S->st));
+    const size_t nb = std::max(bytes, S->tab_bytes * 2);
+    S_TRY(cudaMallocAsync((void**)&S->d_tab, nb, S->st));
+    S->tab_bytes = nb;
+    return RRS_OK;
+}
+
+rrs_status admit(rrs_server* S)
+{
+    std::vector<SlotDev> news;
+    std::vector<int32_t> idx;
+    while (!S->pending.empty()) {
+        Request* R = S->pending.front();
+        if ((int64_t)S->free_slots.size() < R->nq) break;
+        int row = 0;
+        rrs_status s = ensure_dataset(S, R->dataset, &row);
+        if (s != RRS_OK) return s;
+        const DsDev& D = S->ds_host[row];
+        const size_t esz = R->dtype == RRS_F32 ? 4 : 8;
+        const size_t zbytes = esz * (size_t)R->nq * D.d;
+        S_TRY(cudaMallocAsync(&R->zdev, zbytes, S->st));
+        S_TRY(cudaMallocAsync((void**)&R->ddev, sizeof(double) * R->nq, S->st));
+        S_TRY(cudaMemcpyAsync(R->zdev, R->Zhost, zbytes, cudaMemcpyHostToDevice, S->st));
+        for (int64_t q = 0; q < R->nq; ++q) {
+            const int32_t slot = S->free_slots.back();
+            S->free_slots.pop_back();
+            R->slots.push_back(slot);
+            SlotDev sd{};
+            sd.ds = row;
+            sd.kind = R->kind;
+            sd.m = R->m;
+            sd.r = R->r;
+            sd.alpha = R->alpha;
+            sd.d = D.d;
+            sd.ldx = D.ldx;
+            sd.zdtype = R->dtype;
+            sd.seed = R->seed;
+            sd.qctr = q;
+            sd.uoff = (int64_t)slot * S->max_m * S->max_ldx;
+            sd.roff = (int64_t)slot * S->max_m;
+            sd.zoff32 = (int64_t)slot * S->max_ldx;
+            sd.zoff64 = (int64_t)slot * S->max_d;
+            sd.zsrc = (const char*)R->zdev + (size_t)q * D.d * esz;
+            sd.depth_out = R->ddev + q;
+            news.push_back(sd);
+            idx.push_back(slot);
+        }
+        S->pending.pop_front();
+        S->active.push_back(R);
+        S->active_queries += (int)R->nq;
+    }
+    if (news.empty()) return RRS_OK;
+    const size_t b1 = sizeof(SlotDev) * news.size(), b2 = sizeof(int32_t) * idx.size();
+    char* tmp = nullptr;
+    S_TRY(cudaMallocAsync((void**)&tmp, b1 + 256 + b2, S->st));
+    S_TRY(cudaMemcpyAsync(tmp, news.data(), b1, cudaMemcpyHostToDevice, S->st));
+    S_TRY(cudaMemcpyAsync(tmp + b1 + 256 - (b1 % 256), idx.data(), b2, cudaMemcpyHostToDevice, S->st));
+    const int cnt = (int)news.size();
+    k_admit<<<(cnt + 127) / 128, 128, 0, S->st>>>((const SlotDev*)tmp, (const int32_t*)(tmp + b1 + 256 - (b1 % 256)),
+                                                 cnt, S->d_slots, S->d_ds, S->d_z32, S->d_z64, S->d_p0);
+    S_TRY(cudaGetLastError());
+    S->ctx->launches++;
+    S_TRY(cudaFreeAsync(tmp, S->st));
+    return RRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_per_round, int32_t max_d,
+                             void* stream, rrs_server** out)
+{
+    if (!ctx || !out || max_slots < 1 || max_dirs_per_round < 1 || max_d < 1 || max_d > 1024)
+        return sfail(RRS_ERR_INVALID_ARG, "bad server parameters");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    S_TRY(cudaSetDevice(ctx->device));
+    rrs_server* S = new rrs_server;
+    S->ctx = ctx;
+    S->st = (cudaStream_t)stream;
+    S->cap = max_slots;
+    S->max_m = max_dirs_per_round;
+    S->max_d = max_d;
+    S->max_ldx = padded(max_d);
+    S->ds_cap = 4096;
+    const size_t c = (size_t)max_slots;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    const size_t o_slots = take(sizeof(SlotDev) * c), o_z32 = take(sizeof(float) * c * S->max_ldx),
+                 o_p0 = take(sizeof(float) * c * S->max_ldx), o_p1 = take(sizeof(float) * c * S->max_ldx),
+                 o_z64 = take(sizeof(double) * c * max_d), o_U = take(sizeof(float) * c * S->max_m * S->max_ldx),
+                 o_yz = take(sizeof(double) * c * S->max_m), o_res = take(sizeof(ResDev) * c * S->max_m),
+                 o_ds = take(sizeof(DsDev) * S->ds_cap);
+    if (ctx->budget && ctx->used + off > ctx->budget) {
+        delete S;
+        return sfail(RRS_ERR_BUDGET, "server arena needs %zu bytes", off);
+    }
+    cudaError_t e = cudaMalloc(&S->arena, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return sfail(RRS_ERR_CUDA, "server arena: %s", cudaGetErrorString(e));
+    }
+    ctx->used += off;
+    S->arena_bytes = off;
+    char* B = (char*)S->arena;
+    S->d_slots = (SlotDev*)(B + o_slots);
+    S->d_z32 = (float*)(B + o_z32);
+    S->d_p0 = (float*)(B + o_p0);
+    S->d_p1 = (float*)(B + o_p1);
+    S->d_z64 = (double*)(B + o_z64);
+    S->d_U = (float*)(B + o_U);
+    S->d_yz = (double*)(B + o_yz);
+    S->d_res = (ResDev*)(B + o_res);
+    S->d_ds = (DsDev*)(B + o_ds);
+    for (int i = max_slots - 1; i >= 0; --i) S->free_slots.push_back(i);
+    *out = S;
+    return RRS_OK;
+}
+
+rrs_status rrs_server_submit(rrs_server* S, int64_t dataset_id, const void* Z, int64_t n_queries, int32_t dtype,
+                             int32_t kind, int32_t n_dirs, int32_t n_refinements, double cap_shrink, uint64_t seed,
+                             double* depth_out, int64_t* request_id_out)
+{
+    if (!S || !request_id_out || n_queries < 1 || !Z || !depth_out) return sfail(RRS_ERR_INVALID_ARG, "bad request");
+    if (kind < 0 || kind > 2 || n_refinements < 1 || n_dirs < n_refinements || !(cap_shrink > 0.0) ||
+        cap_shrink > 1.0 || (dtype != RRS_F32 && dtype != RRS_F64))
+        return sfail(RRS_ERR_INVALID_ARG, "bad request parameters");
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    auto it = S->ctx->datasets.find(dataset_id);
+    if (it == S->ctx->datasets.end()) return sfail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)dataset_id);
+    const int m = (n_dirs + n_refinements - 1) / n_refinements;
+    if (m > S->max_m || it->second.d > S->max_d || n_queries > S->cap)
+        return sfail(RRS_ERR_UNSUPPORTED, "request exceeds the server's slot shape (m=%d, d=%d, nq=%lld)", m,
+                     it->second.d, (long long)n_queries);
+    if (kind != RRS_HALFSPACE && pdap_max_group((int)it->second.n, it->second.ldx, m) == 0)
+        return sfail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
+    Request* R = new Request;
+    R->id = S->next_id++;
+    R->dataset = dataset_id;
+    R->Zhost = Z;
+    R->nq = n_queries;
+    R->dtype = dtype;
+    R->kind = kind;
+    R->k = n_dirs;
+    R->r = n_refinements;
+    R->m = m;
+    R->alpha = (float)cap_shrink;
+    R->seed = seed;
+    R->out_host = depth_out;
+    S->pending.push_back(R);
+    S->requests[R->id] = R;
+    *request_id_out = R->id;
+    return RRS_OK;
+}
+
+rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* pending_requests_out)
+{
+    if (!S) return sfail(RRS_ERR_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    S_TRY(cudaSetDevice(S->ctx->device));
+    rrs_status s = admit(S);
+    if (s != RRS_OK) return s;
+    if (!S->active.empty()) {
+        // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
+        std::vector<TaskDev> gen, hd;
+        std::map<std::tuple<size_t, int, int>, std::vector<TaskDev>> pd;
+        std::vector<int32_t> arg;
+        const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
+        for (Request* R : S->active) {
+            const DsDev& D = S->ds_host[S->ds_index[R->dataset]];
+            int G = 0;
+            size_t cls = 0;
+            if (R->kind != RRS_HALFSPACE) {
+                G = pdap_max_group((int)D.n, D.ldx, R->m);
+                const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
+                for (size_t c : classes)
+                    if (need <= c) {
+                        cls = c;
+                        break;
+                    }
+            }
+            const int hper = (R->m + ((R->m + 63) / 64) - 1) / ((R->m + 63) / 64);
+            for (int32_t slot : R->slots) {
+                for (int j0 = 0; j0 < R->m; j0 += 128) gen.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
+                if (R->kind == RRS_HALFSPACE) {
+                    for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
+                } else {
+                    auto& v = pd[std::make_tuple(cls, G, pdap_dp4_class(D.d))];
+                    for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), 0});
+                }
+                arg.push_back(slot);
+            }
+        }
+        size_t need = sizeof(TaskDev) * (gen.size() + hd.size()) + sizeof(int32_t) * arg.size() + 1024;
+        for (auto& kv : pd) need += sizeof(TaskDev) * kv.second.size() + 256;
+        s = step_table(S, need);
+        if (s != RRS_OK) return s;
+        std::vector<char> host(need);
+        size_t off = 0;
+        auto put = [&](const void* p, size_t bytes) {
+            const size_t at = off;
+            memcpy(host.data() + off, p, bytes);
+            off = (off + bytes + 255) & ~(size_t)255;
+            return at;
+        };
+        const size_t o_gen = put(gen.data(), sizeof(TaskDev) * gen.size());
+        const size_t o_hd = put(hd.data(), sizeof(TaskDev) * hd.size());
+        const size_t o_arg = put(arg.data(), sizeof(int32_t) * arg.size());
+        std::vector<std::pair<size_t, std::tuple<size_t, int, int>>> o_pd;
+        for (auto& kv : pd) o_pd.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
+        S_TRY(cudaMemcpyAsync(S->d_tab, host.data(), off, cudaMemcpyHostToDevice, S->st));
+        char* T = S->d_tab;
+        S_TRY(launch_gen_slotround((const TaskDev*)(T + o_gen), (int)gen.size(), S->d_slots, S->d_p0, S->d_p1,
+                                   S->d_z64, S->d_U, S->d_yz, S->st));
+        S_TRY(launch_hd_simt((const TaskDev*)(T + o_hd), (int)hd.size(), S->max_ldx, S->d_slots, S->d_ds, S->d_U,
+                             S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err, S->st));
+        for (auto& po : o_pd) {
+            const auto& key = po.second;
+            S_TRY(launch_pdap((const TaskDev*)(T + po.first), (int)pd[key].size(), std::get<0>(key), std::get<1>(key),
+                              std::get<2>(key), S->d_slots, S->d_ds, S->d_U, S->d_z32, S->d_res, S->ctx->d_err,
+                              S->st));
+        }
+        S_TRY(launch_argmin_slotround(S->d_slots, (const int32_t*)(T + o_arg), (int)arg.size(), S->d_U, S->d_res,
+                                     S->d_p0, S->d_p1, S->st));
+        S->ctx->launches += 3 + pd.size();
+        // retire requests whose last round just ran
+        std::vector<Request*> still;
+        for (Request* R : S->active) {
+            R->rounds_done++;
+            if (R->rounds_done == R->r) {
+                S_TRY(cudaMemcpyAsync(R->out_host, R->ddev, sizeof(double) * R->nq, cudaMemcpyDeviceToHost, S->st));
+                S_TRY(cudaEventCreateWithFlags(&R->done, cudaEventDisableTiming));
+                S_TRY(cudaEventRecord(R->done, S->st));
+                S_TRY(cudaFreeAsync(R->zdev, S->st));
+                S_TRY(cudaFreeAsync(R->ddev, S->st));
+                R->zdev = nullptr;
+                R->ddev = nullptr;
+                for (int32_t slot : R->slots) S->free_slots.push_back(slot);
+                S->active_queries -= (int)R->nq;
+                R->finished = true;
+            } else {
+                still.push_back(R);
+            }
+        }
+        S->active.swap(still);
+    }
+    if (active_queries_out) *active_queries_out = S->active_queries;
+    if (pending_requests_out) *pending_requests_out = (int32_t)S->pending.size();
+    return RRS_OK;
+}
+
+rrs_status rrs_server_poll(rrs_server* S, int64_t request_id, int32_t* done_out)
+{
+    if (!S || !done_out) return sfail(RRS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    auto it = S->requests.find(request_id);
+    if (it == S->requests.end()) return sfail(RRS_ERR_NOT_FOUND, "no request %lld", (long long)request_id);
+    Request* R = it->second;
+    *done_out = 0;
+    if (!R->finished) return RRS_OK;
+    const cudaError_t e = cudaEventQuery(R->done);
+    if (e == cudaErrorNotReady) return RRS_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(RRS_ERR_CUDA, "request event: %s", cudaGetErrorString(e));
+    }
+    cudaEventDestroy(R->done);
+    S->requests.erase(it);
+    delete R;
+    *done_out = 1;
+    return RRS_OK;
+}
+
+rrs_status rrs_server_destroy(rrs_server* S)
+{
+    if (!S) return RRS_OK;
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    cudaSetDevice(S->ctx->device);
+    cudaStreamSynchronize(S->st);
+    for (auto& kv : S->requests) {
+        Request* R = kv.second;
+        if (R->zdev) cudaFree(R->zdev);
+        if (R->ddev) cudaFree(R->ddev);
+        if (R->done) cudaEventDestroy(R->done);
+        delete R;
+    }
+    if (S->d_tab) cudaFree(S->d_tab);
+    cudaFree(S->arena);
+    S->ctx->used -= S->arena_bytes;
+    delete S;
+    return RRS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+"""Serving loop (continuous batching) on the GPU.
+
+Requests are admitted into a fixed pool of query slots as slots free up and
+each step runs one refinement round for every active query, so requests that
+arrive while others are in flight share the same launches.  A request's depths
+must not depend on the mix: they must equal rrs_depth on that request alone,
+bit for bit, whether it was served alone, between others, or after waiting for
+slots; one halfspace request is also checked against the CPU oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2506_08262_gb300 as rrs
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from __graft_entry__ import build
+    build()
+    ctx = rrs.Context(0)
+    datasets = []
+    for i, P in enumerate(workloads.c4(seed=51, n_datasets=5, n_lo=200, n_hi=4000, q_hi=40)):
+        did = ctx.register(torch.from_numpy(P.X).cuda())
+        datasets.append((did, P))
+    yield ctx, datasets
+    for did, _ in datasets:
+        ctx.free(did)
+    ctx.close()
+
+
+K, R, ALPHA = 120, 4, 0.8
+
+
+def serve(ctx, batches, max_slots=4096):
+    """batches: list (one per step) of lists of (dataset_id, Z, kind, seed) to submit before that step."""
+    srv = rrs.rrs_server_create(ctx.handle, max_slots, -(-K // R), 100, torch.cuda.current_stream())
+    results, pending = [], {}
+    try:
+        step = 0
+        while step < len(batches) or pending:
+            if step < len(batches):
+                for did, Z, kind, seed in batches[step]:
+                    out = np.full(Z.shape[0], -1.0)
+                    rid = rrs.rrs_server_submit(srv, did, Z, Z.shape[0], rrs.RRS_F32, kind, K, R, ALPHA, seed, out)
+                    pending[rid] = out
+                    results.append(out)
+            rrs.rrs_server_step(srv)
+            for rid in list(pending):
+                if rrs.rrs_server_poll(srv, rid):
+                    del pending[rid]
+            step += 1
+            assert step < 10_000
+        torch.cuda.synchronize()
+        rrs.rrs_check(ctx.handle, torch.cuda.current_stream())
+    finally:
+        rrs.rrs_server_destroy(srv)
+    return results
+
+
+def alone_depth(ctx, did, Z, kind, seed):
+    dep, _, _ = ctx.depth(did, torch.from_numpy(Z).cuda(), kind, K, R, ALPHA, seed)
+    return dep.cpu().numpy()
+
+
+def test_same_result_alone_and_in_the_mix(setup):
+    ctx, ds = setup
+    rng = np.random.default_rng(0)
+    target = (ds[2][0], np.ascontiguousarray(ds[2][1].Z[:7]), 1, 99)
+    others = []
+    for i in range(12):
+        did, P = ds[i % len(ds)]
+        q = int(rng.integers(1, P.nq + 1))
+        others.append((did, np.ascontiguousarray(P.Z[:q]), i % 3, 1000 + i))
+    a = serve(ctx, [[target]])[0]
+    # the target arrives at step 2, while earlier requests are mid-flight, and more follow
+    mix = serve(ctx, [others[:4], others[4:6], [target] + others[6:9], others[9:]])
+    b = mix[6]
+    ref = alone_depth(ctx, target[0], target[1], target[2], target[3])
+    np.testing.assert_array_equal(a, ref)
+    np.testing.assert_array_equal(b, ref)
+    # every request of the mix equals its alone result
+    flat = others[:4] + others[4:6] + [target] + others[6:9] + others[9:]
+    for (did, Z, kind, seed), got in zip(flat, mix):
+        np.testing.assert_array_equal(got, alone_depth(ctx, did, Z, kind, seed))
+
+
+def test_requests_wait_for_slots(setup):
+    ctx, ds = setup
+    reqs = []
+    for i in range(10):
+        did, P = ds[i % len(ds)]
+        reqs.append((did, np.ascontiguousarray(P.Z[: min(P.nq, 20)]), i % 3, 7 + i))
+    got = serve(ctx, [reqs], max_slots=40)   # far fewer slots than queries: requests queue
+    for (did, Z, kind, seed), g in zip(reqs, got):
+        np.testing.assert_array_equal(g, alone_depth(ctx, did, Z, kind, seed))
+
+
+def test_served_halfspace_matches_oracle(setup):
+    ctx, ds = setup
+    did, P = ds[0]
+    Z = np.ascontiguousarray(P.Z[:5])
+    got = serve(ctx, [[(did, Z, 0, 5)]])[0]
+    ref = oracle.rrs(P.X, Z, 0, K, R, ALPHA, 5)
+    np.testing.assert_array_equal(got, ref["depth"])
+
+
+def test_oversize_request_is_rejected(setup):
+    ctx, ds = setup
+    did, P = ds[0]
+    srv = rrs.rrs_server_create(ctx.handle, 4, 30, 100, torch.cuda.current_stream())
+    try:
+        Z = np.ascontiguousarray(P.Z[:5])
+        with pytest.raises(rrs.RRSError) as e:
+            rrs.rrs_server_submit(srv, did, Z, 5, rrs.RRS_F32, 0, K, R, ALPHA, 0, np.zeros(5))
+        assert e.value.status == rrs.RRS_ERR_UNSUPPORTED
+    finally:
+        rrs.rrs_server_destroy(srv)
