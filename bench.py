@@ -51,10 +51,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
                          "c4: 256 datasets batched in one graph-captured launch sequence")
-    ap.add_argument("--scale", type=float, default=1.0, help="c4: shrink n and query counts (tests)")
+    ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="c5: Poisson arrival rate (requests/s)")
+    ap.add_argument("--window", type=float, default=3.0, help="c5: arrival window (s)")
     return ap.parse_args()
 
 
@@ -514,6 +516,135 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD_C5 = ("serving: 64 resident datasets as in the batched workload, Poisson arrivals, 1..4096 queries per "
+               "request (log-uniform), kinds 50/30/20 halfspace/projection/asymmetric, k=1000 over r=10, FP32")
+
+
+def _latency_stats(lat):
+    lat = np.sort(np.asarray(lat))
+    if lat.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "mean_ms": None}
+    return {"p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+            "mean_ms": 1000 * float(lat.mean())}
+
+
+def run_c5(args):
+    """Poisson request stream through the continuous-batching server, against one rrs_depth call per
+    request in arrival order.  Requests that would push the backlog of waiting queries beyond a bound are
+    shed (counted) in both arms."""
+    import collections
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    datasets, reqs = workloads.c5(rate=args.rate, window_s=args.window, scale=args.scale)
+    ctx = rrs.rrs_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    ids = [rrs.rrs_register_dataset(ctx, torch.from_numpy(X).to(dev), X.shape[0], X.shape[1], rrs.RRS_F32, True)
+           for X in datasets]
+    k, r, alpha = 1000, 10, 0.9
+    max_slots = 16384
+    backlog_limit = 2 * max_slots
+
+    # warm the kernels
+    w = rrs.rrs_server_create(ctx, 256, 100, 100, stream)
+    tmp = np.zeros(4)
+    rid = rrs.rrs_server_submit(w, ids[0], reqs[0].Z[:4], 4, rrs.RRS_F32, 1, k, r, alpha, 0, tmp)
+    while not rrs.rrs_server_poll(w, rid):
+        rrs.rrs_server_step(w)
+    rrs.rrs_server_destroy(w)
+    torch.cuda.synchronize()
+
+    # ---- continuous batching ----------------------------------------------------------------
+    srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream)
+    outs, lat, shed, served_q = {}, [], 0, 0
+    inflight = collections.deque()
+    backlog = 0
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(reqs) or outs:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].t_arrival <= now:
+            q = reqs[i]
+            nq = q.Z.shape[0]
+            if backlog + nq > backlog_limit:
+                shed += 1
+            else:
+                out = np.empty(nq)
+                rid = rrs.rrs_server_submit(srv, ids[q.dataset], q.Z, nq, rrs.RRS_F32, q.kind, k, r, alpha, i, out)
+                outs[rid] = (q.t_arrival, nq, out)
+                backlog += nq
+            i += 1
+        if outs:
+            rrs.rrs_server_step(srv)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            inflight.append(ev)
+            if len(inflight) > 2:
+                inflight.popleft().synchronize()
+        elif i < len(reqs):
+            time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)))
+        for rid in list(outs):
+            if rrs.rrs_server_poll(srv, rid):
+                ta, nq, _ = outs.pop(rid)
+                lat.append(time.perf_counter() - t0 - ta)
+                backlog -= nq
+                served_q += nq
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    rrs.rrs_server_destroy(srv)
+    rrs.rrs_check(ctx, stream)
+    cb = {"served_requests": len(lat), "shed_requests": shed, "queries": served_q,
+          "value": served_q / wall, "wall_s": wall, **_latency_stats(lat)}
+
+    # ---- one rrs_depth call per request, arrival order ------------------------------------------
+    lat2, shed2, served2 = [], 0, 0
+    queue = collections.deque()
+    t0 = time.perf_counter()
+    i = 0
+    backlog = 0
+    while i < len(reqs) or queue:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].t_arrival <= now:
+            nq = reqs[i].Z.shape[0]
+            if backlog + nq > backlog_limit:
+                shed2 += 1
+            else:
+                queue.append(i)
+                backlog += nq
+            i += 1
+        if not queue:
+            time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)) if i < len(reqs) else 0)
+            continue
+        j = queue.popleft()
+        q = reqs[j]
+        nq = q.Z.shape[0]
+        out = np.empty(nq)
+        rrs.rrs_depth(ctx, ids[q.dataset], q.Z, nq, rrs.RRS_F32, False, q.kind, k, r, alpha, j,
+                      rrs.RRS_PREC_FP32_SIMT, out, None, None, None, False, stream)
+        lat2.append(time.perf_counter() - t0 - q.t_arrival)
+        backlog -= nq
+        served2 += nq
+    wall2 = time.perf_counter() - t0
+    pr = {"served_requests": len(lat2), "shed_requests": shed2, "queries": served2, "value": served2 / wall2,
+          "wall_s": wall2, **_latency_stats(lat2)}
+    for did in ids:
+        rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    line = {"metric": METRIC, "value": cb["value"], "unit": "query-depths/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1000 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_C5, "rate_req_per_s": args.rate, "window_s": args.window,
+                       "requests_offered": len(reqs), "scale": args.scale, "slots": max_slots,
+                       "backlog_limit_queries": backlog_limit},
+            "continuous_batching": cb, "one_call_per_request": pr, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -522,6 +653,8 @@ def main():
         run_c3(args)
     elif args.workload == "c4":
         run_c4(args)
+    elif args.workload == "c5":
+        run_c5(args)
     else:
         run_ours(args)
 
