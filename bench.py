@@ -60,6 +60,22 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_over_ranks(step_ms: float, device=None) -> float:
+    """Slowest rank's time (all_reduce MAX); the rank's own time when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return step_ms
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, step_ms: float) -> float:
+    """Whole-job throughput: every rank processes its own replica of the work (weak scaling)."""
+    return world * units_per_rank / (step_ms / 1000.0)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,11 +275,7 @@ def run_ours(args):
     launches = rrs.rrs_launch_count(ctx) - launches0
     rrs.rrs_check(ctx, stream)
     clocks = sampler.stop()
-    step_ms = float(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = aggregate_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)) / args.steps, dev)
 
     # end to end through the public API: pinned host query buffer in, host depths out
     Zh = torch.from_numpy(Z).pin_memory()
@@ -286,16 +298,12 @@ def run_ours(args):
         step_e2e()
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_ms = 1000 * float(np.mean(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = aggregate_over_ranks(1000 * float(np.mean(e2e_times)), dev)
     for kd in kinds:
         assert np.array_equal(outh[kd].numpy(), outs[kd].cpu().numpy()), "e2e results differ from device results"
 
     qd_per_step = len(kinds) * nq
-    value = world * qd_per_step / (step_ms / 1000)
+    value = job_value(qd_per_step, world, step_ms)
     pd_per_step = len(kinds) * nq * r * m * n
 
     # roofline of the dominant kernel (selection kernel, plain ALU bound)
@@ -318,7 +326,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (512 MiB device write); inputs smaller than L2"},
         "pd_per_s": world * pd_per_step / (step_ms / 1000),
         "gpu_launches": int(launches),
-        "e2e": {"value": world * qd_per_step / (e2e_ms / 1000), "unit": UNIT,
+        "e2e": {"value": job_value(qd_per_step, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(Zh.numel() * 4 * len(kinds)),
                 "d2h_bytes_per_step": int(nq * 8 * len(kinds))},
         "roofline": {"bound": "alu", "kernel": "k_pdap", "achieved": achieved, "peak": peak, "unit": "Gop/s",

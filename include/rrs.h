@@ -197,6 +197,14 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
  * or rrs_depth_batched. */
 rrs_status rrs_check(rrs_ctx* ctx, void* stream);
 
+/*
+ * rrs_debug_wait_timeout - exercise the failure path of the bounded device
+ * waits: one thread waits on an mbarrier that nothing completes, gives up after
+ * limit_cycles SM clock cycles and flags a timeout.  Returns RRS_ERR_TIMEOUT
+ * (the expected outcome) with the context left usable.  Synchronous.
+ */
+rrs_status rrs_debug_wait_timeout(rrs_ctx* ctx, int64_t limit_cycles);
+
 /* Number of kernel launches this context has issued (for accounting). */
 uint64_t rrs_launch_count(rrs_ctx* ctx);
 

@@ -84,6 +84,7 @@ _SIGS = {
                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "rrs_profile_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
@@ -248,6 +249,10 @@ def rrs_server_poll(server: int, request_id: int) -> bool:
 
 def rrs_server_destroy(server: int) -> None:
     _check(load().rrs_server_destroy(server), "rrs_server_destroy")
+
+
+def rrs_debug_wait_timeout(ctx: int, limit_cycles: int) -> None:
+    _check(load().rrs_debug_wait_timeout(ctx, limit_cycles), "rrs_debug_wait_timeout")
 
 
 def rrs_check(ctx: int, stream=None) -> None:

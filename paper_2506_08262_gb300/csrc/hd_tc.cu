@@ -479,7 +479,29 @@ size_t tc_smem_bytes(int kp)
            (size_t)tc_stages(kp) * 2 * nchunk * plane_bytes_rows(BN);
 }
 
+// Failure-path check: one thread waits on an mbarrier that nothing will complete,
+// with the same bounded wait as the tensor-core kernel but a caller-set limit.
+__global__ void k_wait_probe(int* err, long long limit_cycles)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long t0 = clock64();
+    bool ok = false;
+    while (!(ok = mbar_test(&bar, 0))) {
+        if (clock64() - t0 > limit_cycles) break;
+    }
+    if (!ok) atomicOr(err, ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int* err, long long limit_cycles, cudaStream_t st)
+{
+    k_wait_probe<<<1, 32, 0, st>>>(err, limit_cycles);
+    return cudaGetLastError();
+}
 
 float band_gamma_tc(int kp)
 {

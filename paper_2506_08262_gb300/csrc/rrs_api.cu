@@ -423,6 +423,7 @@ rrs_status check_device_errors(rrs_ctx* ctx, cudaStream_t st)
     if (h) {
         cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
         cudaStreamSynchronize(st);
+        if (h & ERR_TIMEOUT) return fail(RRS_ERR_TIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", h);
         return fail(RRS_ERR_INTERNAL, "device-side error flags 0x%x", h);
     }
     return RRS_OK;
@@ -904,6 +905,22 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
     }
     cudaFree(ws);
     return s;
+}
+
+rrs_status rrs_debug_wait_timeout(rrs_ctx* ctx, int64_t limit_cycles)
+{
+    if (!ctx || limit_cycles < 0) return fail(RRS_ERR_INVALID_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    CUDA_TRY(launch_wait_probe(ctx->d_err, (long long)limit_cycles, 0));
+    ctx->launches++;
+    int h = 0;
+    CUDA_TRY(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    if (h & ERR_TIMEOUT) return fail(RRS_ERR_TIMEOUT, "bounded device wait gave up after %lld cycles",
+                                     (long long)limit_cycles);
+    return RRS_OK;
 }
 
 rrs_status rrs_check(rrs_ctx* ctx, void* stream)

@@ -132,5 +132,6 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots,
                          const DsDev& ds_host, const float* U, const double* yz, const double* z64, ResDev* res,
                          int64_t* band_out, int* err, cudaStream_t st);
 bool hd_tc_supported(int d);
+cudaError_t launch_wait_probe(int* err, long long limit_cycles, cudaStream_t st);
 
 }  // namespace rrs

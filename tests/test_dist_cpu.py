@@ -1,0 +1,63 @@
+"""Multi-rank logic of bench.py on CPU (gloo, world size 2).
+
+The path shards by query with no data exchange, so N GPUs run N replicas; the
+benchmark's only cross-rank step is taking the slowest rank's time and scaling
+the work by N.  These tests run that logic on two gloo ranks.
+"""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WORKER = r'''
+import os, sys, json
+sys.path.insert(0, os.environ["ROOT"])
+import torch.distributed as dist
+dist.init_process_group("gloo")
+import bench
+rank = dist.get_rank()
+ms = 10.0 + 5.0 * rank
+agg = bench.aggregate_over_ranks(ms)
+val = bench.job_value(2000, dist.get_world_size(), agg)
+print(json.dumps({"rank": rank, "agg": agg, "value": val}), flush=True)
+dist.barrier()
+dist.destroy_process_group()
+'''
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    port = free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, ROOT=ROOT, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", WORKER], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err
+        outs.append(out.strip().splitlines()[-1])
+    import json
+    res = [json.loads(o) for o in outs]
+    for r in res:
+        assert r["agg"] == 15.0                     # max over ranks
+        assert r["value"] == pytest.approx(2 * 2000 / 0.015)
+
+
+def test_reference_arm_only_rank0_runs(tmp_path):
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""

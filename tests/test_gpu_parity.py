@@ -275,3 +275,14 @@ def test_budget_is_enforced():
         c.register(torch.from_numpy(X))
     assert e.value.status == rrs.RRS_ERR_BUDGET
     c.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(ctx):
+    # a device wait on a barrier nothing completes gives up (about 1 ms of SM clock) and reports it
+    with pytest.raises(rrs.RRSError) as e:
+        rrs.rrs_debug_wait_timeout(ctx.handle, 2_000_000)
+    assert e.value.status == rrs.RRS_ERR_TIMEOUT
+    X, Z = workloads.gaussian_cloud(3, 100, 3, 2, dtype=np.float32)
+    g = gpu_rrs(ctx, X, Z, H, 30, 2, 0.5)
+    ref = oracle.rrs(X, Z, H, 30, 2, 0.5)
+    np.testing.assert_array_equal(g["count"], ref["count"])
