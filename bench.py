@@ -241,6 +241,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    tuned = {workloads.KIND_NAMES[kd]: rrs.rrs_autotune(ctx, did, kd, k, r) for kd in kinds}
+
     def step():
         for kd in kinds:
             rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F32, True, kd, k, r, alpha, seed, rrs.RRS_PREC_FP32_SIMT,
@@ -323,7 +325,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": qd_per_step * world, "queries_per_kind": nq,
                    "n": n, "d": d, "k": k, "r": r, "alpha": alpha, "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed steps (512 MiB device write); inputs smaller than L2"},
+                   "l2": "flushed between timed steps (512 MiB device write); inputs smaller than L2",
+                   "autotuned_directions_per_cta": tuned},
         "pd_per_s": world * pd_per_step / (step_ms / 1000),
         "gpu_launches": int(launches),
         "e2e": {"value": job_value(qd_per_step, world, e2e_ms), "unit": UNIT,

@@ -161,6 +161,20 @@ typedef struct rrs_request {
 rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_requests,
                              int32_t use_graph, void* stream);
 
+/*
+ * rrs_autotune - pick the selection kernel's directions per CTA (1, 2 or 4)
+ * for projection / asymmetric projection depth on this dataset with m =
+ * ceil(n_dirs / n_refinements) directions per round: each feasible choice is
+ * timed on one round of probe queries (rows of the dataset, two per SM) and the
+ * fastest is cached in the context; later rrs_depth / rrs_depth_batched calls
+ * with the same (n, d, m) use it.  Without tuning a shared-memory heuristic
+ * decides.  Results never depend on the choice.  *choice_out (optional)
+ * receives it (0 for halfspace depth, which has nothing to tune).
+ * Synchronous.  Errors: INVALID_ARG, NOT_FOUND, CUDA.
+ */
+rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,
+                        int32_t* choice_out);
+
 /* Text for a status code (static storage). */
 const char* rrs_status_string(rrs_status status);
 

@@ -84,6 +84,8 @@ _SIGS = {
                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_autotune": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                      ctypes.c_void_p], ctypes.c_int32),
     "rrs_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
@@ -253,6 +255,13 @@ def rrs_server_destroy(server: int) -> None:
 
 def rrs_debug_wait_timeout(ctx: int, limit_cycles: int) -> None:
     _check(load().rrs_debug_wait_timeout(ctx, limit_cycles), "rrs_debug_wait_timeout")
+
+
+def rrs_autotune(ctx: int, dataset_id: int, kind: int, n_dirs: int, n_refinements: int) -> int:
+    """Time the selection kernel's group sizes for this (dataset, kind, m) and cache the fastest."""
+    choice = ctypes.c_int32()
+    _check(load().rrs_autotune(ctx, dataset_id, kind, n_dirs, n_refinements, ctypes.byref(choice)), "rrs_autotune")
+    return choice.value
 
 
 def rrs_check(ctx: int, stream=None) -> None:

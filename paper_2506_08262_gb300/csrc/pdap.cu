@@ -40,7 +40,8 @@ struct Ctl {
     int cnt[MAXG][2];                  // keys in the run
     int fill[MAXG][2];                 // keys gathered so far
     int fb[MAXG];                      // 1: fall back for all statistics, 2: only MAD_+
-    float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: bucket((y - lo_b) * sc_y)
+    float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: about (y - lo_b) * sc_y
+    float off_y[MAXG];                 // -lo_b * sc_y (bucket_fma offset)
     float scale[MAXG];                 // sigma_u (or the radius) of each direction
     float cen[MAXG], sc_d[MAXG];       // bucket map of |y - med| (D_P)
     float v1[MAXG][2], v2[MAXG][2];    // selected order statistics
@@ -59,6 +60,14 @@ __device__ __forceinline__ int bucket(float y, float lo, float scale)
     // (y - lo) * scale, rounded once, truncated: monotone in y
     const int b = __float2int_rz(__fmul_rn(__fsub_rn(y, lo), scale));
     return b < 0 ? 0 : (b > NB - 1 ? NB - 1 : b);
+}
+
+// Bucket of the pass maps: y*sc + off rounded once, truncated (negatives saturate to 0),
+// clamped to the last bucket.  Monotone non-decreasing in y.
+__device__ __forceinline__ int bucket_fma(float y, float sc, float off)
+{
+    const unsigned b = __float2uint_rz(__fmaf_rn(y, sc, off));
+    return b < (unsigned)(NB - 1) ? (int)b : NB - 1;
 }
 
 __device__ __forceinline__ float warp_max(float v)
@@ -282,44 +291,62 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
         C.yz[g] = a;
         C.lo_b[g] = yc - half;
         C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
+        C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
     }
     __syncthreads();
 
     // ---- pass A: keys + bucket counts ----------------------------------------------
     {
-        float lo[G], sc[G];
+        float of[G], sc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            lo[g] = C.lo_b[g];
+            of[g] = C.off_y[g];
             sc[g] = C.sc_y[g];
         }
+        auto emit = [&](int i, const float (&acc)[G]) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                keys[(size_t)g * npad + i] = acc[g];
+                atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
+            }
+        };
         if (DP4 > 0) {
             float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
                 for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
-            for (int i = tid; i < n; i += NT) {
-                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-                float acc[G];
-#pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = 0.f;
+            // two points per iteration: both rows' loads are in flight together
+            for (int i = tid; i < n; i += 2 * NT) {
+                const int i2 = i + NT;
+                const bool two = i2 < n;
+                const float4* xa = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                const float4* xb = reinterpret_cast<const float4*>(D.X32 + (int64_t)(two ? i2 : i) * ldx);
+                float4 va[DP4 > 0 ? DP4 / 4 : 1], vb[DP4 > 0 ? DP4 / 4 : 1];
 #pragma unroll
                 for (int c = 0; c < DP4 / 4; ++c) {
-                    const float4 x = xr[c];
+                    va[c] = xa[c];
+                    vb[c] = xb[c];
+                }
+                float acc[G], acc2[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = acc2[g] = 0.f;
+#pragma unroll
+                for (int c = 0; c < DP4 / 4; ++c) {
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        acc[g] = fmaf(ur[g][c].x, x.x, acc[g]);
-                        acc[g] = fmaf(ur[g][c].y, x.y, acc[g]);
-                        acc[g] = fmaf(ur[g][c].z, x.z, acc[g]);
-                        acc[g] = fmaf(ur[g][c].w, x.w, acc[g]);
+                        acc[g] = fmaf(ur[g][c].x, va[c].x, acc[g]);
+                        acc[g] = fmaf(ur[g][c].y, va[c].y, acc[g]);
+                        acc[g] = fmaf(ur[g][c].z, va[c].z, acc[g]);
+                        acc[g] = fmaf(ur[g][c].w, va[c].w, acc[g]);
+                        acc2[g] = fmaf(ur[g][c].x, vb[c].x, acc2[g]);
+                        acc2[g] = fmaf(ur[g][c].y, vb[c].y, acc2[g]);
+                        acc2[g] = fmaf(ur[g][c].z, vb[c].z, acc2[g]);
+                        acc2[g] = fmaf(ur[g][c].w, vb[c].w, acc2[g]);
                     }
                 }
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    keys[(size_t)g * npad + i] = acc[g];
-                    atomicAdd(&hist[g * NB + bucket(acc[g], lo[g], sc[g])], 1u);
-                }
+                emit(i, acc);
+                if (two) emit(i2, acc2);
             }
         } else {
             for (int i = tid; i < n; i += NT) {
@@ -338,11 +365,7 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
                         acc[g] = fmaf(u.w, x.w, acc[g]);
                     }
                 }
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    keys[(size_t)g * npad + i] = acc[g];
-                    atomicAdd(&hist[g * NB + bucket(acc[g], lo[g], sc[g])], 1u);
-                }
+                emit(i, acc);
             }
         }
     }
@@ -388,35 +411,44 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
     // ---- pass C: gather the runs ------------------------------------------------
     {
         int bl0[G], bw0[G], bl1[G], bw1[G];
-        float lo[G], sc[G];
+        float of[G], sc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             // a run that is off gets a start no bucket index can reach: (b - start) is then
             // never <= 0 as an unsigned number
             const bool on = !C.fb[g];
-            lo[g] = C.lo_b[g];
+            of[g] = C.off_y[g];
             sc[g] = C.sc_y[g];
             bl0[g] = on ? C.b_lo[g][0] : (1 << 30);
             bw0[g] = on ? C.b_hi[g][0] - C.b_lo[g][0] : 0;
             bl1[g] = (ap && on) ? C.b_lo[g][1] : (1 << 30);
             bw1[g] = (ap && on) ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
         }
-        for (int i = tid; i < n; i += NT) {
+        auto gather = [&](int g, float y) {
+            const int b = bucket_fma(y, sc[g], of[g]);
+            if ((unsigned)(b - bl0[g]) <= (unsigned)bw0[g]) {
+                const int pos = atomicAdd(&C.fill[g][0], 1);
+                if (pos < CAP) buf[(g * 2 + 0) * CAP + pos] = y;
+            }
+            if (ap && (unsigned)(b - bl1[g]) <= (unsigned)bw1[g]) {
+                const int pos = atomicAdd(&C.fill[g][1], 1);
+                if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = y;
+            }
+        };
+        const int n4 = n & ~3;
+        for (int i = 4 * tid; i < n4; i += 4 * NT) {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                {
-                    const float y = keys[(size_t)g * npad + i];
-                    const int b = bucket(y, lo[g], sc[g]);
-                    if ((unsigned)(b - bl0[g]) <= (unsigned)bw0[g]) {
-                        const int pos = atomicAdd(&C.fill[g][0], 1);
-                        if (pos < CAP) buf[(g * 2 + 0) * CAP + pos] = y;
-                    }
-                    if (ap && (unsigned)(b - bl1[g]) <= (unsigned)bw1[g]) {
-                        const int pos = atomicAdd(&C.fill[g][1], 1);
-                        if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = y;
-                    }
-                }
+                const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
+                gather(g, y4.x);
+                gather(g, y4.y);
+                gather(g, y4.z);
+                gather(g, y4.w);
             }
+        }
+        for (int i = n4 + tid; i < n; i += NT) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) gather(g, keys[(size_t)g * npad + i]);
         }
     }
     __syncthreads();
@@ -492,14 +524,27 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
                 cen[g] = C.cen[g];
                 scl[g] = C.sc_d[g];
             }
-            for (int i = tid; i < n; i += NT) {
+            auto add = [&](int g, float y) {
+                const float dv = fabsf(__fsub_rn(y, cen[g]));
+                atomicAdd(&hist[g * NB + bucket_fma(dv, scl[g], 0.0f)], 1u);
+            };
+            const int n4 = n & ~3;
+            for (int i = 4 * tid; i < n4; i += 4 * NT) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     if (on[g]) {
-                        const float dv = fabsf(__fsub_rn(keys[(size_t)g * npad + i], cen[g]));
-                        atomicAdd(&hist[g * NB + bucket(dv, 0.0f, scl[g])], 1u);
+                        const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
+                        add(g, y4.x);
+                        add(g, y4.y);
+                        add(g, y4.z);
+                        add(g, y4.w);
                     }
                 }
+            }
+            for (int i = n4 + tid; i < n; i += NT) {
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (on[g]) add(g, keys[(size_t)g * npad + i]);
             }
         }
         __syncthreads();
@@ -527,18 +572,28 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
                 bl[g] = !C.fb[g] ? C.b_lo[g][1] : (1 << 30);
                 bw[g] = !C.fb[g] ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
             }
-            for (int i = tid; i < n; i += NT) {
+            auto gather = [&](int g, float y) {
+                const float dv = fabsf(__fsub_rn(y, cen[g]));
+                const int b = bucket_fma(dv, scl[g], 0.0f);
+                if ((unsigned)(b - bl[g]) <= (unsigned)bw[g]) {
+                    const int pos = atomicAdd(&C.fill[g][1], 1);
+                    if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = dv;
+                }
+            };
+            const int n4 = n & ~3;
+            for (int i = 4 * tid; i < n4; i += 4 * NT) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    {
-                        const float dv = fabsf(__fsub_rn(keys[(size_t)g * npad + i], cen[g]));
-                        const int b = bucket(dv, 0.0f, scl[g]);
-                        if ((unsigned)(b - bl[g]) <= (unsigned)bw[g]) {
-                            const int pos = atomicAdd(&C.fill[g][1], 1);
-                            if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = dv;
-                        }
-                    }
+                    const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
+                    gather(g, y4.x);
+                    gather(g, y4.y);
+                    gather(g, y4.z);
+                    gather(g, y4.w);
                 }
+            }
+            for (int i = n4 + tid; i < n; i += NT) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) gather(g, keys[(size_t)g * npad + i]);
             }
         }
         __syncthreads();

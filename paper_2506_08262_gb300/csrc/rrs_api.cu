@@ -151,6 +151,9 @@ struct Plan {
     int64_t tot_ldx = 0, tot_d = 0, tot_u = 0, tot_m = 0;
     bool any_tc = false;
     int precision = RRS_PREC_FP32_SIMT;
+    // selection-kernel group size: autotuned choices and an explicit override (tuning probes)
+    const std::map<std::tuple<int64_t, int, int>, int>* tune = nullptr;
+    int force_group = 0;
     // device pointers (after carving)
     DsDev* d_ds = nullptr;
     SlotDev* d_slots = nullptr;
@@ -249,7 +252,13 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             return fail(RRS_ERR_UNSUPPORTED, "FP32 halfspace kernel stages 128 rows of d floats; d=%d too large", D.d);
         if (R.kind != RRS_HALFSPACE) {
             if (D.n > 0x7FFFFFFF) return fail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
-            G = pdap_max_group((int)D.n, D.ldx, m);
+            G = P.force_group;
+            if (!G && P.tune) {
+                auto it = P.tune->find(std::make_tuple(D.n, D.ldx, m));
+                if (it != P.tune->end()) G = it->second;
+            }
+            if (G && (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())) G = 0;
+            if (!G) G = pdap_max_group((int)D.n, D.ldx, m);
             if (G == 0)
                 return fail(RRS_ERR_UNSUPPORTED,
                             "projection depth needs n*4 bytes of shared memory per direction; n=%lld is too large",
@@ -596,9 +605,12 @@ static rrs_status ensure_bf16_planes(rrs_ctx* ctx, Dataset& D)
     return RRS_OK;
 }
 
-static rrs_status run_requests(rrs_ctx* ctx, std::vector<ReqView>& reqs, int precision, cudaStream_t st)
+static rrs_status run_requests(rrs_ctx* ctx, std::vector<ReqView>& reqs, int precision, cudaStream_t st,
+                               int force_group = 0)
 {
     Plan P;
+    P.tune = &ctx->pd_tune;
+    P.force_group = force_group;
     rrs_status s = build_plan(reqs, precision, P);
     if (s != RRS_OK) return s;
     if (P.slots.empty()) return RRS_OK;
@@ -754,6 +766,7 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
         }
     }
     Plan P;
+    P.tune = &ctx->pd_tune;
     rrs_status s = build_plan(views, RRS_PREC_FP32_SIMT, P);
     if (s != RRS_OK) return s;
     Carve sizing;
@@ -921,6 +934,79 @@ rrs_status rrs_debug_wait_timeout(rrs_ctx* ctx, int64_t limit_cycles)
     if (h & ERR_TIMEOUT) return fail(RRS_ERR_TIMEOUT, "bounded device wait gave up after %lld cycles",
                                      (long long)limit_cycles);
     return RRS_OK;
+}
+
+rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,
+                        int32_t* choice_out)
+{
+    if (!ctx) return fail(RRS_ERR_INVALID_ARG, "NULL context");
+    rrs_status s = validate_params(kind, n_dirs, n_refinements, 0.5, RRS_F32, RRS_PREC_FP32_SIMT);
+    if (s != RRS_OK) return s;
+    if (choice_out) *choice_out = 0;
+    if (kind == RRS_HALFSPACE) return RRS_OK;   // nothing to tune on this path
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->datasets.find(dataset_id);
+    if (it == ctx->datasets.end()) return fail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)dataset_id);
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    Dataset& D = it->second;
+    const int m = (n_dirs + n_refinements - 1) / n_refinements;
+    const auto key = std::make_tuple(D.n, D.ldx, m);
+    // probe queries: the first rows of the data cloud, 2 per SM
+    int nsm = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int64_t nq = std::min<int64_t>(D.n, 2 * (int64_t)nsm);
+    std::vector<float> rows((size_t)nq * D.ldx), zh((size_t)nq * D.d);
+    CUDA_TRY(cudaMemcpy(rows.data(), D.X32, sizeof(float) * rows.size(), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < nq; ++q)
+        for (int l = 0; l < D.d; ++l) zh[(size_t)q * D.d + l] = rows[(size_t)q * D.ldx + l];
+    float* zd = nullptr;
+    CUDA_TRY(cudaMalloc(&zd, sizeof(float) * zh.size()));
+    CUDA_TRY(cudaMemcpy(zd, zh.data(), sizeof(float) * zh.size(), cudaMemcpyHostToDevice));
+    double* dep = nullptr;
+    CUDA_TRY(cudaMalloc(&dep, sizeof(double) * nq));
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int G : {1, 2, 4}) {
+        if (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit()) continue;
+        ReqView R{};
+        R.dset = &D;
+        R.Z = zd;
+        R.nq = nq;
+        R.dtype = RRS_F32;
+        R.kind = kind;
+        R.k = m;
+        R.r = 1;
+        R.alpha = 0.5f;
+        R.depth_out = dep;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            std::vector<ReqView> reqs{R};
+            CUDA_TRY(cudaEventRecord(a, 0));
+            s = run_requests(ctx, reqs, RRS_PREC_FP32_SIMT, 0, G);
+            if (s != RRS_OK) break;
+            CUDA_TRY(cudaEventRecord(b, 0));
+            CUDA_TRY(cudaEventSynchronize(b));
+            float ms = 0.0f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0) t = std::min(t, ms);   // first repetition warms up
+        }
+        if (s != RRS_OK) break;
+        if (!best || t < best_ms) {
+            best = G;
+            best_ms = t;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(zd);
+    cudaFree(dep);
+    if (s != RRS_OK) return s;
+    if (best) ctx->pd_tune[key] = best;
+    if (choice_out) *choice_out = best;
+    return check_device_errors(ctx, 0);
 }
 
 rrs_status rrs_check(rrs_ctx* ctx, void* stream)

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/rrs.h"
@@ -48,6 +49,8 @@ struct rrs_ctx {
         size_t launches = 0;
     };
     std::vector<GraphEntry> graphs;
+    // selection-kernel autotuning: (n, ldx, m) -> directions per CTA
+    std::map<std::tuple<int64_t, int, int>, int> pd_tune;
     // per-stage CUDA-event timing (rrs_profile_*)
     bool profiling = false;
     struct Mark {

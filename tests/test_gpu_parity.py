@@ -286,3 +286,16 @@ def test_bounded_wait_reports_timeout_and_context_survives(ctx):
     g = gpu_rrs(ctx, X, Z, H, 30, 2, 0.5)
     ref = oracle.rrs(X, Z, H, 30, 2, 0.5)
     np.testing.assert_array_equal(g["count"], ref["count"])
+
+
+@pytest.mark.parametrize("kind", [P, AP])
+def test_autotuned_group_does_not_change_results(ctx, kind):
+    X, Z = workloads.gaussian_cloud(31, 5000, 10, 30, dtype=np.float32)
+    did = ctx.register(torch.from_numpy(X).cuda())
+    Zt = torch.from_numpy(Z).cuda()
+    before = ctx.depth(did, Zt, kind, 100, 4, 0.7, 3)[0].cpu().numpy()
+    g = rrs.rrs_autotune(ctx.handle, did, kind, 100, 4)
+    assert g in (1, 2, 4)
+    after = ctx.depth(did, Zt, kind, 100, 4, 0.7, 3)[0].cpu().numpy()
+    ctx.free(did)
+    np.testing.assert_array_equal(before, after)
