@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
     ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
@@ -341,6 +342,9 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed": wall,
     }
+    if rank == 0 and world == 1 and not args.no_halfspace:
+        # secondary: the tensor-core halfspace path against the FP32 path (d=50 workload, 1,000 queries)
+        line["halfspace_d50"] = measure_halfspace(1000, 2, 3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample_rate(max(1, os.cpu_count() or 1))
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
@@ -358,15 +362,14 @@ WORKLOAD_C3 = ("halfspace depth, d=50, n=100000 Student-t(3) rows mapped by a ra
                "10000 queries from the same law, k=2000 dirs over r=20 rounds, alpha=0.9, FP32 data")
 
 
-def run_c3(args):
-    """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path."""
+def measure_halfspace(nq: int, steps: int, warmup: int):
+    """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path on `nq`
+    queries of the d=50 workload (full n, k, r).  Returns a dict with both arms and the speedup."""
     import torch
-    from __graft_entry__ import build
-    build()
     import paper_2506_08262_gb300 as rrs
     dev = torch.device("cuda", 0)
-    P = workloads.c3(nq=args.nq or 10_000)
-    n, d, nq, k, r = P.n, P.d, P.nq, P.k, P.r
+    P = workloads.c3(nq=nq)
+    n, d, k, r = P.n, P.d, P.k, P.r
     m = -(-k // r)
     ctx = rrs.rrs_create(0, 0)
     did = rrs.rrs_register_dataset(ctx, torch.from_numpy(P.X).to(dev), n, d, rrs.RRS_F32, True)
@@ -379,8 +382,7 @@ def run_c3(args):
     except OSError:
         pass
     bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-    out = {}
-    results = {}
+    out, results = {}, {}
     for name, prec in (("tc", rrs.RRS_PREC_SPLIT_BF16X3), ("fp32", rrs.RRS_PREC_FP32_SIMT)):
         dep = torch.empty(nq, dtype=torch.float64, device=dev)
         cnt = torch.empty(nq, dtype=torch.int64, device=dev)
@@ -388,7 +390,7 @@ def run_c3(args):
         def step():
             rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F32, True, rrs.RRS_HALFSPACE, k, r, P.alpha, P.seed, prec,
                           dep, cnt, None, None, True, stream)
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(3, warmup)):
             step()
         rrs.rrs_check(ctx, stream)
         torch.cuda.synchronize()
@@ -396,7 +398,7 @@ def run_c3(args):
         sampler.start()
         rrs.rrs_profile_enable(ctx, True)
         evs = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -408,7 +410,7 @@ def run_c3(args):
         rrs.rrs_profile_enable(ctx, False)
         clocks = sampler.stop()
         rrs.rrs_check(ctx, stream)
-        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
         stage = "hd_tc" if prec == rrs.RRS_PREC_SPLIT_BF16X3 else "hd_simt"
         kms, kl = prof[stage]
         elems_per_launch = nq * m * n
@@ -430,20 +432,29 @@ def run_c3(args):
             entry["roofline"] = {"bound": "alu", "kernel": "k_hd_simt", "achieved": achieved, "peak": peak,
                                  "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                                  "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x 2070 MHz"}
-        results[name] = (dep.cpu().numpy(), cnt.cpu().numpy())
+        results[name] = cnt.cpu().numpy()
         out[name] = entry
-    assert np.array_equal(results["tc"][1], results["fp32"][1]), "tensor-core and FP32 counts differ"
-    line = {"metric": METRIC, "value": out["tc"]["value"], "unit": "query-depths/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": out["tc"]["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD_C3, "n": n, "d": d, "queries": nq, "k": k, "r": r,
-                       "l2": "flushed between timed steps (512 MiB device write)"},
-            "tensor_core": out["tc"], "fp32_cuda_core": out["fp32"],
-            "speedup_tc_over_fp32": out["fp32"]["ms_per_step"] / out["tc"]["ms_per_step"],
-            "counts_identical": True}
+    same = bool(np.array_equal(results["tc"], results["fp32"]))
     rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
+    return {"workload": WORKLOAD_C3, "queries": nq, "n": n, "d": d, "k": k, "r": r, "tensor_core": out["tc"],
+            "fp32_cuda_core": out["fp32"], "speedup_tc_over_fp32": out["fp32"]["ms_per_step"] / out["tc"]["ms_per_step"],
+            "counts_identical": same}
+
+
+def run_c3(args):
+    """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path."""
+    from __graft_entry__ import build
+    build()
+    h = measure_halfspace(args.nq or 10_000, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": h["tensor_core"]["value"], "unit": "query-depths/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": h["tensor_core"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_C3, "n": h["n"], "d": h["d"], "queries": h["queries"], "k": h["k"],
+                       "r": h["r"], "l2": "flushed between timed steps (512 MiB device write)"},
+            **{key: h[key] for key in ("tensor_core", "fp32_cuda_core", "speedup_tc_over_fp32", "counts_identical")}}
+    assert h["counts_identical"], "tensor-core and FP32 counts differ"
     print(json.dumps(line), flush=True)
 
 
