@@ -7,17 +7,21 @@
 // data planes carry 1 in two spare K columns and the direction planes carry
 // the BF16 parts of -u'z there, so the accumulator holds t = u'x - u'z
 // directly.  The epilogue counts t < -b and t > b, b = gamma (|x| + |z|) a
-// bound on the error of t, and re-checks every |t| <= b with the exact FP64
-// sign test, so the counts are exact.
+// bound on the error of t; every |t| <= b is settled by a compensated FP32
+// dot product (about twice FP32 precision) and, when even that is too close
+// to call, by the exact FP64 sign test, so the counts are exact.
 //
 // CTA layout (320 threads): warp 0 streams point tiles with TMA into a
 // 4-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-9 read
-// the accumulator (one direction per TMEM lane, two warps per lane quarter,
-// each taking half of a tile's columns) and count.  The accumulator is double
-// buffered so the epilogue of tile t overlaps the MMAs of tile t+1.  Per
-// 32-column chunk the epilogue first takes min|t| and the sign-bit count; only
-// a chunk whose min|t| reaches the chunk's largest band goes through the
-// per-point band test.
+// the accumulator (one accumulator row per TMEM lane, two warps per lane
+// quarter, each taking half of a tile's columns) and count.  The 128 rows of
+// a CTA are consecutive (query, direction) pairs of one request, so one tile
+// may hold several queries.  Four accumulator buffers let the MMAs run up to
+// three tiles ahead of the epilogue.  Per 32-column chunk the epilogue packs
+// the sign bits of t and of (b - |t|) into bit words (three instructions per
+// column); columns inside the band go to a per-warp queue that is settled 32
+// at a time, one candidate per lane, so the rare slow test never serialises a
+// warp on one point.
 // Every wait on an mbarrier is bounded; on timeout the CTA flags ERR_TIMEOUT
 // and winds down.
 #include <cuda.h>
@@ -37,6 +41,8 @@ namespace {
 constexpr int BM = 128;          // directions per CTA (TMEM lanes)
 constexpr int BN = 128;          // points per tile (accumulator columns)
 constexpr int STAGES = 4;
+constexpr int NACC = 4;                      // accumulator buffers in tensor memory (4 x 128 columns)
+constexpr int QCAP = 64;                     // near-tie queue entries per epilogue warp
 constexpr int NEPI = 8;                      // epilogue warps: two per TMEM lane quarter
 constexpr int NTHREADS = 64 + 32 * NEPI;
 
@@ -124,20 +130,25 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes (one row per thread);
+// the registers are valid only after tmem_wait_ld / tmem_order
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// wait for this thread's outstanding tcgen05.ld; the registers are in-out operands so no
+// use of them can be scheduled before the wait
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
+}
+// orders later uses of r after the preceding volatile asm (a second load's registers)
+__device__ __forceinline__ void tmem_order(uint32_t (&r)[32])
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) : : "memory");
 }
 
 // byte offset of element (row, k) in a K chunk of 64 BF16 per row, 128-byte swizzle
@@ -151,31 +162,114 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_us
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
 struct TcShared {
-    uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+    uint64_t full[STAGES], empty[STAGES], acc_full[NACC], acc_empty[NACC];
     uint32_t tmem_base;
     int abort;
     int mma_tiles;   // tiles whose operands the MMA issuer has consumed
+    unsigned zmax_bits;
 };
+
+// One accumulator row of the CTA: a (query, direction) pair.
+struct RowInfo {
+    long long uoff;   // element offset of the direction's FP32 row in U
+    int roff;         // index of (query, direction) in y_z and in the results
+    int zoff64;       // offset of the query's FP64 row
+    float zn;         // |z|, rounded up
+    float yh, yl;     // y_z = u'z as an unevaluated FP32 pair (|y_z - yh - yl| <= 2^-48 |y_z|)
+    int slot;         // query slot (index of the near-tie counter)
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// Sign of t = u'x - y_z from a compensated FP32 dot product (error-free products and
+// sums, errors gathered in a second float), i.e. t to about twice FP32 precision.
+// Returns +1 / -1, or 0 when |t| does not clear twice the bound and the caller must
+// take the exact test.  u and x are ldx-long rows (zero padded, 16-byte aligned).
+__device__ __noinline__ int ff_sign(const float* __restrict__ u, const float* __restrict__ x, int ldx, float yh,
+                                    float yl, float bound)
+{
+    float s = 0.f, c = 0.f;
+    auto acc = [&](float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);   // exact: a b = p + pe
+        float s2, se;
+        two_sum_f(s, p, s2, se);
+        s = s2;
+        c = __fadd_rn(c, __fadd_rn(se, pe));
+    };
+    for (int l = 0; l < ldx; l += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(u + l);
+        const float4 b = *reinterpret_cast<const float4*>(x + l);
+        acc(a.x, b.x);
+        acc(a.y, b.y);
+        acc(a.z, b.z);
+        acc(a.w, b.w);
+    }
+    float a, ea;
+    two_sum_f(s, -yh, a, ea);
+    const float t = __fadd_rn(a, __fadd_rn(ea, __fsub_rn(c, yl)));
+    const float b2 = __fmul_rn(2.0f, bound);
+    if (t > b2) return 1;
+    if (t < -b2) return -1;
+    return 0;
+}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_hd_tc(const __grid_constant__ CUtensorMap xmap, const TaskDev* __restrict__ tasks,
             const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets, const float* __restrict__ U,
             const double* __restrict__ yz, const double* __restrict__ z64, ResDev* __restrict__ res,
-            int64_t* __restrict__ band_out, int* err, float gamma, int nst)
+            int64_t* __restrict__ band_out, int* err, float gamma, float ffcoef, int nst)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ TcShared sh;
-    __shared__ float xnW[NEPI][32];
+    __shared__ RowInfo rows[BM];
+    __shared__ __align__(16) float bcol[NEPI][64];            // per-column band bound of the current tile
+    __shared__ uint32_t qpt[NEPI][QCAP];                      // candidate queue: point index
+    __shared__ uint8_t qrow[NEPI][QCAP];                      //                  accumulator row
+    __shared__ int cand_lt[BM], cand_gt[BM];                  // exact verdicts on candidates, per row
     __shared__ long long partial_lt[NEPI][32], partial_gt[NEPI][32];
 
     if (*(volatile const int*)err & ERR_TIMEOUT) return;   // another CTA already gave up
     const TaskDev T = tasks[blockIdx.x];
-    const SlotDev& S = slots[T.slot];
-    const DsDev D = dsets[S.ds];
-    const int kp = D.kp, nchunk = kp / 64, d = D.d;
+    const DsDev D = dsets[slots[T.slot].ds];
+    const int kp = D.kp, nchunk = kp / 64, d = D.d, ldx = D.ldx;
     const int64_t n = D.n;
     const int ntiles = (int)((n + BN - 1) / BN);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // ---- rows: T covers rows j0 .. j0+nj-1 of its request's (query, direction) sequence,
+    //      m directions per query, starting at query slot T.slot -------------------------
+    if (threadIdx.x == 0) sh.zmax_bits = 0u;
+    __syncthreads();
+    if (threadIdx.x < BM) {
+        const int r = threadIdx.x;
+        RowInfo ri{};
+        if (r < T.nj) {
+            const int m = slots[T.slot].m;
+            const int gg = T.j0 + r;
+            const int qs = gg / m, j = gg - qs * m;
+            const SlotDev& S = slots[T.slot + qs];
+            ri.uoff = S.uoff + (long long)j * S.ldx;
+            ri.roff = S.roff + j;
+            ri.zoff64 = S.zoff64;
+            ri.zn = S.znorm;
+            ri.slot = T.slot + qs;
+            const double y = yz[ri.roff];
+            ri.yh = (float)y;
+            ri.yl = (float)(y - (double)ri.yh);
+            atomicMax(&sh.zmax_bits, __float_as_uint(S.znorm));
+        }
+        rows[r] = ri;
+        cand_lt[r] = 0;
+        cand_gt[r] = 0;
+    }
+    __syncthreads();
 
     // 1024-byte aligned operand area: A planes (hi, lo) then STAGES x B planes (hi, lo)
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -190,13 +284,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int r = e / kp, k = e - r * kp;
         float hi = 0.f, lo = 0.f;
         if (r < T.nj) {
-            const int j = T.j0 + r;
             if (k < d) {
-                const float u = U[S.uoff + (int64_t)j * S.ldx + k];
+                const float u = U[rows[r].uoff + k];
                 hi = bf16_val(bf16_bits(u));
                 lo = u - hi;   // exact in FP32
             } else if (k == d || k == d + 1) {
-                const double y = yz[S.roff + j];
+                const double y = yz[rows[r].roff];
                 const float y1 = bf16_val(bf16_bits((float)y));
                 const double r1 = y - (double)y1;
                 const float y2 = bf16_val(bf16_bits((float)r1));
@@ -224,7 +317,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sh.empty[s], 1);
         }
         sh.mma_tiles = 0;
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&sh.acc_full[b], 1);
             mbar_init(&sh.acc_empty[b], NEPI);   // one arrival per epilogue warp
         }
@@ -233,7 +326,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
-                     "r"(2 * BN)
+                     "r"(NACC * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -273,9 +366,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
             for (int t = 0; t < ntiles; ++t) {
-                const int s = t % nst, b = t & 1;
+                const int s = t % nst, b = t % NACC;
                 if (!mbar_wait(&sh.full[s], (t / nst) & 1, err) ||
-                    (t >= 2 && !mbar_wait(&sh.acc_empty[b], ((t >> 1) - 1) & 1, err))) {
+                    (t >= NACC && !mbar_wait(&sh.acc_empty[b], ((t / NACC) - 1) & 1, err))) {
                     atomicOr(err, ERR_TIMEOUT);
                     sh.abort = 1;
                     break;
@@ -308,109 +401,135 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (*(volatile int*)&sh.abort && done > 0) {
                 // let the last issued MMAs finish before tensor memory is released
                 const int t = done - 1;
-                mbar_wait(&sh.acc_full[t & 1], (t >> 1) & 1, err, false);
+                mbar_wait(&sh.acc_full[t % NACC], (t / NACC) & 1, err, false);
             }
         }
     } else {
-        // ---- epilogue: one direction per thread -------------------------------------------------
+        // ---- epilogue: one accumulator row (direction) per thread ---------------------------
+        // Fast path per 32 columns: the sign bits of t and of (bound - |t|) are packed into
+        // bit words, so a column costs one add and two funnel shifts; the few columns inside
+        // the band go to a per-warp queue and are settled 32 at a time, one per lane.
         const int e = warp - 2;                 // 0..NEPI-1
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int half = e >> 2;                // which half of the tile's columns
-        const int row = q * 32 + lane;          // direction row = TMEM lane
+        const int row = q * 32 + lane;          // accumulator row = TMEM lane
         const bool live = row < T.nj;
-        const int j = T.j0 + row;
-        const float gzn = gamma * S.znorm;
-        const float* ujs = U + S.uoff + (int64_t)(live ? j : T.j0) * S.ldx;
-        const double* zrow = z64 + S.zoff64;
-        const float yz32 = (float)yz[S.roff + (live ? j : T.j0)];
-        const float g32 = band_gamma_fp32(d);
-        int64_t lt = 0, gt = 0, nband = 0;
+        const float gz = gamma * __uint_as_float(sh.zmax_bits);
+        const double* X64 = D.X64;
+        long long lt = 0, gt = 0;
+        int qn = 0;                             // queue fill (warp-uniform)
+
+        // settle queue entries [b0, b0 + cnt): lane k takes entry b0 + k
+        auto settle = [&](int b0, int cnt) {
+            __syncwarp();
+            if (lane < cnt) {
+                const int64_t i = qpt[e][b0 + lane];
+                const int r = qrow[e][b0 + lane];
+                const RowInfo& R = rows[r];
+                const float* ur = U + R.uoff;
+                int sgn;
+                if (X64) {
+                    sgn = rrsdev::exact_sign<double>(ur, 1, X64 + i * d, z64 + R.zoff64, d, err);
+                } else {
+                    const float* xr = D.X32 + i * ldx;
+                    const float bnd = ffcoef * (D.xnorm[i] + R.zn) + (float)(d + 2) * 0x1p-140f;
+                    sgn = ff_sign(ur, xr, ldx, R.yh, R.yl, bnd);
+                    if (sgn == 0) sgn = rrsdev::exact_sign<float>(ur, 1, xr, z64 + R.zoff64, d, err);
+                }
+                if (sgn < 0) atomicAdd(&cand_lt[r], 1);
+                else if (sgn > 0) atomicAdd(&cand_gt[r], 1);
+                if (band_out) atomicAdd((unsigned long long*)&band_out[R.slot], 1ull);
+            }
+            __syncwarp();
+        };
+        // count one 32-column chunk; candidates (|t| <= bound, or t not a number) are queued
+        auto chunk = [&](const uint32_t (&v)[32], int cc, int64_t c0) {
+            const int64_t nv = n - c0;
+            uint32_t vmask = nv >= 32 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : ~(0xFFFFFFFFu >> (int)nv));   // bit 31-k: column k
+            if (!live) vmask = 0u;
+            uint32_t sw[4] = {0u, 0u, 0u, 0u}, bw[4] = {0u, 0u, 0u, 0u};
+            const float4* bq = reinterpret_cast<const float4*>(&bcol[e][cc * 32]);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const float4 B4 = bq[g];
+                const float Bk[4] = {B4.x, B4.y, B4.z, B4.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int k = g * 4 + h, w = k >> 3;
+                    sw[w] = __funnelshift_l(v[k], sw[w], 1);                     // sign of t
+                    const float dl = __fsub_rn(Bk[h], fabsf(__uint_as_float(v[k])));
+                    bw[w] = __funnelshift_l(__float_as_uint(dl), bw[w], 1);      // set: |t| > bound
+                }
+            }
+            const uint32_t sa = (sw[0] << 24) | (sw[1] << 16) | (sw[2] << 8) | sw[3];
+            const uint32_t ba = ((bw[0] << 24) | (bw[1] << 16) | (bw[2] << 8) | bw[3]) & vmask;
+            const int neg = __popc(sa & ba);
+            lt += neg;
+            gt += __popc(ba) - neg;
+            uint32_t cm = vmask & ~ba;
+            unsigned bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
+            while (bal) {
+                const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                if (cm) {
+                    const int k = __clz(cm);
+                    cm &= ~(0x80000000u >> k);
+                    qpt[e][pos] = (uint32_t)(c0 + k);
+                    qrow[e][pos] = (uint8_t)row;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) {
+                    settle(qn - 32, 32);
+                    qn -= 32;
+                }
+                bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
+            }
+        };
+
+        auto xload = [&](int t, int cc) -> float {
+            const int64_t c = (int64_t)t * BN + half * 64 + cc * 32 + lane;
+            return (t < ntiles && c < n) ? D.xnorm[c] : 0.0f;
+        };
+        float xa0 = xload(0, 0), xa1 = xload(0, 1);
+        bool aborted = false;
         for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
-            const int64_t col0 = (int64_t)t * BN;
+            const int b = t % NACC;
+            const float xb0 = xload(t + 1, 0), xb1 = xload(t + 1, 1);   // next tile's norms, in flight
             // one lane waits, the whole warp follows its verdict (tcgen05.ld needs the full warp)
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&sh.acc_full[b], (t >> 1) & 1, err) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&sh.acc_full[b], (t / NACC) & 1, err) ? 1 : 0;
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-            __syncwarp();
             if (!ok) {
                 if (lane == 0) {
                     atomicOr(err, ERR_TIMEOUT);
                     sh.abort = 1;
                 }
+                aborted = true;
                 break;
             }
             tc_fence_after();
-            const int valid = (n - col0 < BN) ? (int)(n - col0) : BN;
-#pragma unroll 1
-            for (int cc = 0; cc < BN / 64; ++cc) {
-                const int ch = half * (BN / 64) + cc;
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + ch * 32), v);
-                const int cl = ch * 32 + lane;
-                const float xl = cl < valid ? D.xnorm[col0 + cl] : 0.0f;
-                float xmax = xl;
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) xmax = fmaxf(xmax, __shfl_xor_sync(0xFFFFFFFFu, xmax, o));
-                __syncwarp();
-                xnW[e][lane] = xl;
-                __syncwarp();
-                if (!live) continue;
-                const bool full = ch * 32 + 32 <= valid;
-                if (full) {
-                    float mn = fabsf(v[0]);
-                    uint32_t neg = __float_as_uint(v[0]) >> 31;
-#pragma unroll
-                    for (int k = 1; k < 32; ++k) {
-                        mn = fminf(mn, fabsf(v[k]));
-                        neg += __float_as_uint(v[k]) >> 31;
-                    }
-                    if (mn > fmaf(gamma, xmax, gzn)) {   // no point of the chunk is near a tie
-                        lt += neg;
-                        gt += 32 - neg;
-                        continue;
-                    }
-                }
-                for (int k = 0; k < 32; ++k) {
-                    const int c = ch * 32 + k;
-                    if (c >= valid) break;
-                    const float bnd = fmaf(gamma, xnW[e][k], gzn);
-                    const float tv = v[k];
-                    if (tv < -bnd) {
-                        lt++;
-                    } else if (tv > bnd) {
-                        gt++;
-                    } else {
-                        // second stage: FP32 projection with its own, ~30x narrower, bound;
-                        // only what stays inside goes to the exact FP64 test
-                        const int64_t i = col0 + c;
-                        const float* xr = D.X32 + i * D.ldx;
-                        float t32 = 0.0f;
-                        for (int l = 0; l < d; ++l) t32 = fmaf(ujs[l], xr[l], t32);
-                        t32 = t32 - yz32;
-                        const float b32 = g32 * (xnW[e][k] + S.znorm);
-                        int sgn;
-                        if (t32 > b32) sgn = 1;
-                        else if (t32 < -b32) sgn = -1;
-                        else if (D.X64) sgn = rrsdev::exact_sign<double>(ujs, 1, D.X64 + i * d, zrow, d, err);
-                        else sgn = rrsdev::exact_sign<float>(ujs, 1, xr, zrow, d, err);
-                        lt += (sgn < 0);
-                        gt += (sgn > 0);
-                        nband++;
-                    }
-                }
-            }
+            uint32_t v0[32], v1[32];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 64);
+            tmem_ld32_async(ta, v0);
+            tmem_ld32_async(ta + 32, v1);
+            tmem_wait_ld(v0);
+            tmem_order(v1);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.acc_empty[b]);
+            if (lane == 0) mbar_arrive(&sh.acc_empty[b]);   // the accumulator is in registers now
+            bcol[e][lane] = fmaf(gamma, xa0, gz);
+            bcol[e][32 + lane] = fmaf(gamma, xa1, gz);
+            __syncwarp();
+            const int64_t c0 = (int64_t)t * BN + half * 64;
+            chunk(v0, 0, c0);
+            chunk(v1, 1, c0 + 32);
+            __syncwarp();
+            xa0 = xb0;
+            xa1 = xb1;
         }
+        if (!aborted && qn > 0) settle(0, qn);
         // the two warps of a lane quarter each counted half of the columns
         partial_lt[e][lane] = lt;
         partial_gt[e][lane] = gt;
-        if (band_out) {
-            for (int o = 16; o >= 1; o >>= 1) nband += __shfl_xor_sync(0xFFFFFFFFu, nband, o);
-            if (lane == 0) atomicAdd((unsigned long long*)&band_out[T.slot], (unsigned long long)nband);
-        }
     }
     tc_fence_before();
     __syncthreads();
@@ -418,16 +537,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int e = warp - 2;   // warps e and e + 4 read the same TMEM lanes
         const int row = (warp & 3) * 32 + lane;
         if (row < T.nj && !sh.abort) {
-            const long long l2 = partial_lt[e][lane] + partial_lt[e + 4][lane];
-            const long long g2 = partial_gt[e][lane] + partial_gt[e + 4][lane];
+            const long long l2 = partial_lt[e][lane] + partial_lt[e + 4][lane] + cand_lt[row];
+            const long long g2 = partial_gt[e][lane] + partial_gt[e + 4][lane] + cand_gt[row];
             const int64_t le = n - g2, ge = n - l2;
             const int64_t cmin = le < ge ? le : ge;
-            res[S.roff + T.j0 + row] = ResDev{(double)cmin / (double)n, cmin};
+            res[rows[row].roff] = ResDev{(double)cmin / (double)n, cmin};
         }
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * BN) : "memory");
     }
 }
 
@@ -511,6 +630,15 @@ float band_gamma_tc(int kp)
     return (float)(1.25 * g);
 }
 
+float band_coef_ff(int d)
+{
+    // compensated FP32 dot product of d terms: the rounding errors of the gathered error terms,
+    // at most (2d^2 + 4d + 8) 2^-48 sum|u x|; y_z's FP64 evaluation and its FP32 pair, at most
+    // (d + 8) 2^-52 |u'z|; |u| <= 1 + 2^-20 covered by the 1% slack
+    const double dd = (double)d;
+    return (float)(((2.0 * dd * dd + 4.0 * dd + 8.0) * 0x1p-48 + (dd + 8.0) * 0x1p-52) * 1.01);
+}
+
 bool hd_tc_supported(int d) { return d >= 1 && d + 2 <= 128; }
 
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
@@ -531,6 +659,7 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots,
     if (!enc) return cudaErrorNotSupported;
     const int kp = ds_host.kp;
     if (kp != 64 && kp != 128) return cudaErrorInvalidValue;
+    if (ds_host.n > 0x7FFFFFFF) return cudaErrorInvalidValue;   // point indices and TMA rows are 32-bit
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)(2 * kp), (cuuint64_t)ds_host.n};
     const cuuint64_t gstride[1] = {(cuuint64_t)(2 * kp) * sizeof(uint16_t)};
@@ -547,7 +676,7 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots,
         return e;
     }
     k_hd_tc<<<ntasks, NTHREADS, smem, st>>>(map, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
-                                            band_gamma_tc(kp), tc_stages(kp));
+                                            band_gamma_tc(kp), band_coef_ff(ds_host.d), tc_stages(kp));
     return cudaGetLastError();
 }
 

@@ -271,6 +271,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
                 }
             if (cls < 0) return fail(RRS_ERR_INTERNAL, "no shared-memory class for n=%lld", (long long)D.n);
         }
+        const int s_first = (int)P.slots.size();
         for (int64_t q = 0; q < R.nq; ++q) {
             SlotDev S{};
             S.ds = dsidx[R.dset];
@@ -302,14 +303,24 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             P.max_ldx = std::max(P.max_ldx, D.ldx);
             for (int j0 = 0; j0 < m; j0 += 128) P.gen_tasks.push_back(TaskDev{s, j0, std::min(128, m - j0), 0});
             if (R.kind == RRS_HALFSPACE) {
-                const int cap = precision == RRS_PREC_SPLIT_BF16X3 ? 128 : 64;   // directions per CTA
-                const int nt = (m + cap - 1) / cap;
-                const int per = (m + nt - 1) / nt;
-                for (int j0 = 0; j0 < m; j0 += per) P.hd_tasks.push_back(TaskDev{s, j0, std::min(per, m - j0), 0});
+                if (precision != RRS_PREC_SPLIT_BF16X3) {
+                    const int cap = 64;   // directions per CTA of the FP32 kernel
+                    const int nt = (m + cap - 1) / cap;
+                    const int per = (m + nt - 1) / nt;
+                    for (int j0 = 0; j0 < m; j0 += per) P.hd_tasks.push_back(TaskDev{s, j0, std::min(per, m - j0), 0});
+                }
             } else {
                 for (int j0 = 0; j0 < m; j0 += G) P.pd_tasks[cls].push_back(TaskDev{s, j0, std::min(G, m - j0), 0});
             }
             P.argmin_list.push_back(s);
+        }
+        if (R.kind == RRS_HALFSPACE && precision == RRS_PREC_SPLIT_BF16X3) {
+            // tensor-core tasks: 128 consecutive (query, direction) rows of this request, so the
+            // accumulator's M dimension is filled across queries (task = first query slot, offset
+            // into that query's directions, row count)
+            const int64_t rows = R.nq * (int64_t)m;
+            for (int64_t g = 0; g < rows; g += 128)
+                P.hd_tasks.push_back(TaskDev{s_first + (int)(g / m), (int)(g % m), (int)std::min<int64_t>(128, rows - g), 0});
         }
         P.rmax = std::max(P.rmax, R.r);
     }

@@ -83,6 +83,7 @@ enum : int {
 // (FP64 inputs), of y_z to FP32 and of the final difference; twice that sum for slack.
 __host__ __device__ inline float band_gamma_fp32(int d) { return (float)((double)(d + 4) * 0x1p-23); }
 float band_gamma_tc(int kp);
+float band_coef_ff(int d);   // bound coefficient of the compensated FP32 re-check (tensor-core path)
 
 // Set the text that rrs_last_error() returns on this thread (rrs_api.cu).
 void set_last_error(const char* msg);

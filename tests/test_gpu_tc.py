@@ -87,3 +87,29 @@ def test_tc_round_counts_exact_and_band_sound(ctx):
             assert c[q, j] == oracle.univariate(H, P.X, P.Z[q], U[q, j])[1]
     # band re-checks are a small fraction of all point-direction pairs
     assert int(band.sum()) < 0.02 * 3 * m * P.n
+
+
+@pytest.mark.parametrize("k,r,nq", [(111, 3, 9), (600, 2, 3), (256, 2, 7)])
+def test_tc_rows_span_queries(ctx, k, r, nq):
+    # a CTA's 128 accumulator rows are consecutive (query, direction) pairs: m = 37 packs
+    # several queries per tile, m = 300 starts tiles inside a query, m = 128 fills tiles exactly
+    X, Z = workloads.gaussian_cloud(900 + k, 1000, 50, nq, dtype=np.float32, zscale=1.2)
+    g = run(ctx, X, Z, k, r, 0.8, 21, TC)
+    ref = oracle.rrs(X, Z, H, k, r, 0.8, 21)
+    np.testing.assert_array_equal(g["count"], ref["count"])
+    np.testing.assert_array_equal(g["best"], ref["best"])
+    f = run(ctx, X, Z, k, r, 0.8, 21, rrs.RRS_PREC_FP32_SIMT)
+    np.testing.assert_array_equal(g["choice"], f["choice"])
+
+
+def test_tc_exact_ties_on_a_lattice(ctx):
+    # duplicated lattice points and queries placed on data points: many projection
+    # differences are exactly zero, so the exact fallback decides them
+    rng = np.random.default_rng(8)
+    base = rng.integers(-3, 4, size=(150, 6)).astype(np.float32)
+    X = np.concatenate([base, base[:90], base[:40]]).astype(np.float32)
+    Z = np.concatenate([X[[0, 5, 17, 151]], rng.integers(-3, 4, size=(3, 6)).astype(np.float32)])
+    g = run(ctx, X, Z, 200, 2, 0.6, 4, TC)
+    ref = oracle.rrs(X, Z, H, 200, 2, 0.6, 4)
+    np.testing.assert_array_equal(g["count"], ref["count"])
+    np.testing.assert_array_equal(g["depth"], ref["depth"])
