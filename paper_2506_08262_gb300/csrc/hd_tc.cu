@@ -11,13 +11,15 @@
 // dot product (about twice FP32 precision) and, when even that is too close
 // to call, by the exact FP64 sign test, so the counts are exact.
 //
-// CTA layout (320 threads): warp 0 streams point tiles with TMA into a
-// 4-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-9 read
-// the accumulator (one accumulator row per TMEM lane, two warps per lane
-// quarter, each taking half of a tile's columns) and count.  The 128 rows of
-// a CTA are consecutive (query, direction) pairs of one request, so one tile
-// may hold several queries.  Four accumulator buffers let the MMAs run up to
-// three tiles ahead of the epilogue.  Per 32-column chunk the epilogue packs
+// CTA layout (576 threads): warp 0 streams point tiles with TMA into a
+// 2-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-17 read
+// the accumulator (one accumulator row per TMEM lane, four warps per lane
+// quarter, each taking one 32-column chunk of every tile) and count.  The 128
+// rows of a CTA are consecutive (query, direction) pairs of one request, so
+// one tile may hold several queries.  Tiles are 256 points wide for a K
+// extent of 64 (four accumulator buffers of 128 columns otherwise); two
+// 256-column accumulator buffers let the MMAs of one tile overlap the
+// epilogue of the previous one.  Per chunk the epilogue packs
 // the sign bits of t and of (b - |t|) into bit words (three instructions per
 // column); columns inside the band go to a per-warp queue that is settled 32
 // at a time, one candidate per lane, so the rare slow test never serialises a
@@ -39,22 +41,27 @@ namespace rrs {
 namespace {
 
 constexpr int BM = 128;          // directions per CTA (TMEM lanes)
-constexpr int BN = 128;          // points per tile (accumulator columns)
-constexpr int STAGES = 4;
-constexpr int NACC = 4;                      // accumulator buffers in tensor memory (4 x 128 columns)
+// Points per tile (accumulator columns, the MMA's N) is a template parameter: 256 when the
+// K extent is 64 (a 128 x 256 x 16 MMA runs at the full tensor rate; 128 x 128 x 16 does
+// not), 128 when it is 128 (two 256-point stages would not fit in shared memory).
+constexpr int STAGES = 4;                    // largest TMA ring
+constexpr int MAXACC = 4;                    // accumulator buffers: 512 TMEM columns / BN
 constexpr int QCAP = 64;                     // near-tie queue entries per epilogue warp
-constexpr int NEPI = 8;                      // epilogue warps: two per TMEM lane quarter
+constexpr int NEPI = 16;                     // epilogue warps: four per TMEM lane quarter
 constexpr int NTHREADS = 64 + 32 * NEPI;
 
 __host__ __device__ constexpr int plane_bytes_rows(int rows) { return rows * 128; }   // one 64-wide K chunk
 
 // instruction descriptor of tcgen05.mma kind::f16: BF16 A and B, FP32 accumulator,
-// both operands K-major, M = 128, N = BN
-constexpr uint32_t kIdesc = (1u << 4)                 // D format: FP32
-                            | (1u << 7)               // A format: BF16
-                            | (1u << 10)              // B format: BF16
-                            | ((uint32_t)(BN >> 3) << 17)
-                            | ((uint32_t)(BM >> 4) << 24);
+// both operands K-major, M = 128, N = bn
+__host__ __device__ constexpr uint32_t mma_idesc(int bn)
+{
+    return (1u << 4)                     // D format: FP32
+           | (1u << 7)                   // A format: BF16
+           | (1u << 10)                  // B format: BF16
+           | ((uint32_t)(bn >> 3) << 17)
+           | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -115,11 +122,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar)
@@ -162,7 +170,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_us
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
 struct TcShared {
-    uint64_t full[STAGES], empty[STAGES], acc_full[NACC], acc_empty[NACC];
+    uint64_t full[STAGES], empty[STAGES], acc_full[MAXACC], acc_empty[MAXACC];
     uint32_t tmem_base;
     int abort;
     int mma_tiles;   // tiles whose operands the MMA issuer has consumed
@@ -220,6 +228,7 @@ __device__ __noinline__ int ff_sign(const float* __restrict__ u, const float* __
     return 0;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_hd_tc(const __grid_constant__ CUtensorMap xmap, const TaskDev* __restrict__ tasks,
             const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets, const float* __restrict__ U,
@@ -229,11 +238,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ TcShared sh;
     __shared__ RowInfo rows[BM];
-    __shared__ __align__(16) float bcol[NEPI][64];            // per-column band bound of the current tile
+    constexpr int NACC = 512 / BN;                            // accumulator buffers
+    constexpr int CPW = BN / 128;                             // 32-column chunks per epilogue warp and tile
+    __shared__ __align__(16) float bcol[NEPI][32 * CPW];      // per-column band bound of the warp's chunks
     __shared__ uint32_t qpt[NEPI][QCAP];                      // candidate queue: point index
     __shared__ uint8_t qrow[NEPI][QCAP];                      //                  accumulator row
     __shared__ int cand_lt[BM], cand_gt[BM];                  // exact verdicts on candidates, per row
-    __shared__ long long partial_lt[NEPI][32], partial_gt[NEPI][32];
+    __shared__ uint32_t partial_lt[NEPI][32], partial_gt[NEPI][32];
 
     if (*(volatile const int*)err & ERR_TIMEOUT) return;   // another CTA already gave up
     const TaskDev T = tasks[blockIdx.x];
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         for (int ks = 0; ks < 4; ++ks) {
                             const uint64_t ad = sw128_desc(ap + c * plane_bytes_rows(BM) + ks * 32);
                             const uint64_t bd = sw128_desc(bp + c * plane_bytes_rows(BN) + ks * 32);
-                            umma_bf16(dtm, ad, bd, acc);
+                            umma_bf16(dtm, ad, bd, mma_idesc(BN), acc);
                             acc = 1;
                         }
                     }
@@ -406,17 +417,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ---- epilogue: one accumulator row (direction) per thread ---------------------------
-        // Fast path per 32 columns: the sign bits of t and of (bound - |t|) are packed into
-        // bit words, so a column costs one add and two funnel shifts; the few columns inside
-        // the band go to a per-warp queue and are settled 32 at a time, one per lane.
+        // Four warps share each TMEM lane quarter; warp e takes the 32-column chunk e / 4 of
+        // every tile.  Per column the sign bits of t and of (bound - |t|) are shifted into bit
+        // words (one add and two funnel shifts); the few columns inside the band go to a
+        // per-warp queue that is settled 32 at a time, one candidate per lane.
         const int e = warp - 2;                 // 0..NEPI-1
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = e >> 2;                // which half of the tile's columns
+        const int cw = e >> 2;                  // column chunk of each tile
         const int row = q * 32 + lane;          // accumulator row = TMEM lane
         const bool live = row < T.nj;
         const float gz = gamma * __uint_as_float(sh.zmax_bits);
         const double* X64 = D.X64;
-        long long lt = 0, gt = 0;
+        uint32_t lt = 0, gt = 0;                // n < 2^31
         int qn = 0;                             // queue fill (warp-uniform)
 
         // settle queue entries [b0, b0 + cnt): lane k takes entry b0 + k
@@ -442,58 +454,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             __syncwarp();
         };
-        // count one 32-column chunk; candidates (|t| <= bound, or t not a number) are queued
-        auto chunk = [&](const uint32_t (&v)[32], int cc, int64_t c0) {
-            const int64_t nv = n - c0;
-            uint32_t vmask = nv >= 32 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : ~(0xFFFFFFFFu >> (int)nv));   // bit 31-k: column k
-            if (!live) vmask = 0u;
-            uint32_t sw[4] = {0u, 0u, 0u, 0u}, bw[4] = {0u, 0u, 0u, 0u};
-            const float4* bq = reinterpret_cast<const float4*>(&bcol[e][cc * 32]);
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const float4 B4 = bq[g];
-                const float Bk[4] = {B4.x, B4.y, B4.z, B4.w};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int k = g * 4 + h, w = k >> 3;
-                    sw[w] = __funnelshift_l(v[k], sw[w], 1);                     // sign of t
-                    const float dl = __fsub_rn(Bk[h], fabsf(__uint_as_float(v[k])));
-                    bw[w] = __funnelshift_l(__float_as_uint(dl), bw[w], 1);      // set: |t| > bound
-                }
-            }
-            const uint32_t sa = (sw[0] << 24) | (sw[1] << 16) | (sw[2] << 8) | sw[3];
-            const uint32_t ba = ((bw[0] << 24) | (bw[1] << 16) | (bw[2] << 8) | bw[3]) & vmask;
-            const int neg = __popc(sa & ba);
-            lt += neg;
-            gt += __popc(ba) - neg;
-            uint32_t cm = vmask & ~ba;
-            unsigned bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
-            while (bal) {
-                const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                if (cm) {
-                    const int k = __clz(cm);
-                    cm &= ~(0x80000000u >> k);
-                    qpt[e][pos] = (uint32_t)(c0 + k);
-                    qrow[e][pos] = (uint8_t)row;
-                }
-                qn += __popc(bal);
-                if (qn >= 32) {
-                    settle(qn - 32, 32);
-                    qn -= 32;
-                }
-                bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
-            }
-        };
 
-        auto xload = [&](int t, int cc) -> float {
-            const int64_t c = (int64_t)t * BN + half * 64 + cc * 32 + lane;
-            return (t < ntiles && c < n) ? D.xnorm[c] : 0.0f;
-        };
-        float xa0 = xload(0, 0), xa1 = xload(0, 1);
+        // this lane's column in chunk j of tile t is t * BN + (cw * CPW + j) * 32 + lane; the
+        // norms are prefetched two tiles ahead so the load latency stays off the per-tile path
+        const int cbase = cw * CPW * 32;
+        const float* xp = D.xnorm + cbase + lane;
+        int xrem = (int)n - (cbase + lane);     // > j * 32 while the lane's column of chunk j exists
+        int crem = (int)n - cbase;              // columns left from the warp's first chunk
+        float xa[CPW], xb[CPW];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            xa[j] = xrem > j * 32 ? xp[j * 32] : 0.f;
+            xb[j] = xrem > BN + j * 32 ? xp[BN + j * 32] : 0.f;
+        }
         bool aborted = false;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % NACC;
-            const float xb0 = xload(t + 1, 0), xb1 = xload(t + 1, 1);   // next tile's norms, in flight
+            float xc[CPW];
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) xc[j] = xrem > 2 * BN + j * 32 ? xp[2 * BN + j * 32] : 0.f;
             // one lane waits, the whole warp follows its verdict (tcgen05.ld needs the full warp)
             int ok = 1;
             if (lane == 0) ok = mbar_wait(&sh.acc_full[b], (t / NACC) & 1, err) ? 1 : 0;
@@ -506,39 +485,91 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 aborted = true;
                 break;
             }
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) bcol[e][j * 32 + lane] = fmaf(gamma, xa[j], gz);
             tc_fence_after();
-            uint32_t v0[32], v1[32];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 64);
-            tmem_ld32_async(ta, v0);
-            tmem_ld32_async(ta + 32, v1);
-            tmem_wait_ld(v0);
-            tmem_order(v1);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.acc_empty[b]);   // the accumulator is in registers now
-            bcol[e][lane] = fmaf(gamma, xa0, gz);
-            bcol[e][32 + lane] = fmaf(gamma, xa1, gz);
-            __syncwarp();
-            const int64_t c0 = (int64_t)t * BN + half * 64;
-            chunk(v0, 0, c0);
-            chunk(v1, 1, c0 + 32);
-            __syncwarp();
-            xa0 = xb0;
-            xa1 = xb1;
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) {
+                uint32_t v[32];
+                tmem_ld32_async(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + cbase + j * 32), v);
+                tmem_wait_ld(v);
+                if (j == CPW - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh.acc_empty[b]);   // the accumulator is in registers now
+                } else {
+                    __syncwarp();
+                }
+                const int cr = crem - j * 32;
+                const uint32_t vmask = !live ? 0u : (cr >= 32 ? 0xFFFFFFFFu : (cr <= 0 ? 0u : ~(0xFFFFFFFFu >> cr)));
+                // bit 31-k of a word is column k: two chains of 16 per word for instruction-level parallelism
+                uint32_t s0 = 0u, s1 = 0u, b0 = 0u, b1 = 0u;
+                const float4* bq = reinterpret_cast<const float4*>(&bcol[e][j * 32]);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const float4 B4 = bq[g], C4 = bq[g + 4];
+                    const float Bk[4] = {B4.x, B4.y, B4.z, B4.w};
+                    const float Ck[4] = {C4.x, C4.y, C4.z, C4.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const uint32_t va = v[g * 4 + h], vb = v[16 + g * 4 + h];
+                        s0 = __funnelshift_l(va, s0, 1);
+                        s1 = __funnelshift_l(vb, s1, 1);
+                        b0 = __funnelshift_l(__float_as_uint(__fsub_rn(Bk[h], fabsf(__uint_as_float(va)))), b0, 1);
+                        b1 = __funnelshift_l(__float_as_uint(__fsub_rn(Ck[h], fabsf(__uint_as_float(vb)))), b1, 1);
+                    }
+                }
+                const uint32_t sa = __byte_perm(s1, s0, 0x5410);               // (s0 << 16) | s1
+                const uint32_t ba = __byte_perm(b1, b0, 0x5410) & vmask;        // set: |t| > bound
+                const uint32_t neg = __popc(sa & ba);
+                lt += neg;
+                gt += __popc(ba) - neg;
+                uint32_t cm = vmask & ~ba;                                      // candidates
+                unsigned bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
+                if (bal) {
+                    const uint32_t c0 = (uint32_t)(t * BN + cbase + j * 32);
+                    do {
+                        const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                        if (cm) {
+                            const int k = __clz(cm);
+                            cm &= ~(0x80000000u >> k);
+                            qpt[e][pos] = c0 + (uint32_t)k;
+                            qrow[e][pos] = (uint8_t)row;
+                        }
+                        qn += __popc(bal);
+                        if (qn >= 32) {
+                            settle(qn - 32, 32);
+                            qn -= 32;
+                        }
+                        bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
+                    } while (bal);
+                }
+            }
+            __syncwarp();   // bcol is rewritten next tile
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) {
+                xa[j] = xb[j];
+                xb[j] = xc[j];
+            }
+            xp += BN;
+            xrem -= BN;
+            crem -= BN;
         }
         if (!aborted && qn > 0) settle(0, qn);
-        // the two warps of a lane quarter each counted half of the columns
+        // the four warps of a lane quarter each counted a quarter of the columns
         partial_lt[e][lane] = lt;
         partial_gt[e][lane] = gt;
     }
     tc_fence_before();
     __syncthreads();
     if (warp >= 2 && warp < 6) {
-        const int e = warp - 2;   // warps e and e + 4 read the same TMEM lanes
+        const int e = warp - 2;   // warps e, e + 4, e + 8, e + 12 read the same TMEM lanes
         const int row = (warp & 3) * 32 + lane;
         if (row < T.nj && !sh.abort) {
-            const long long l2 = partial_lt[e][lane] + partial_lt[e + 4][lane] + cand_lt[row];
-            const long long g2 = partial_gt[e][lane] + partial_gt[e + 4][lane] + cand_gt[row];
+            const long long l2 = (long long)partial_lt[e][lane] + partial_lt[e + 4][lane] + partial_lt[e + 8][lane] +
+                                 partial_lt[e + 12][lane] + cand_lt[row];
+            const long long g2 = (long long)partial_gt[e][lane] + partial_gt[e + 4][lane] + partial_gt[e + 8][lane] +
+                                 partial_gt[e + 12][lane] + cand_gt[row];
             const int64_t le = n - g2, ge = n - l2;
             const int64_t cmin = le < ge ? le : ge;
             res[rows[row].roff] = ResDev{(double)cmin / (double)n, cmin};
@@ -589,13 +620,15 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-int tc_stages(int kp) { return kp <= 64 ? STAGES : 2; }
+int tc_tile_n(int kp) { return kp <= 64 ? 256 : 128; }
+
+int tc_stages(int kp) { return 2; }   // 2 x 64 KB (K extent 64, 256 points) or 2 x 64 KB (128, 128 points)
 
 size_t tc_smem_bytes(int kp)
 {
     const size_t nchunk = (size_t)kp / 64;
     return 1024 /* alignment slack */ + 2 * nchunk * plane_bytes_rows(BM) +
-           (size_t)tc_stages(kp) * 2 * nchunk * plane_bytes_rows(BN);
+           (size_t)tc_stages(kp) * 2 * nchunk * plane_bytes_rows(tc_tile_n(kp));
 }
 
 // Failure-path check: one thread waits on an mbarrier that nothing will complete,
@@ -663,20 +696,22 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots,
     CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)(2 * kp), (cuuint64_t)ds_host.n};
     const cuuint64_t gstride[1] = {(cuuint64_t)(2 * kp) * sizeof(uint16_t)};
-    const cuuint32_t box[2] = {64, BN};
+    const int bn = tc_tile_n(kp);
+    const cuuint32_t box[2] = {64, (cuuint32_t)bn};
     const cuuint32_t estride[2] = {1, 1};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ds_host.Xbf, gdim, gstride, box, estride,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes(kp);
-    cudaError_t e = cudaFuncSetAttribute(k_hd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = bn == 256 ? k_hd_tc<256> : k_hd_tc<128>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e;
     }
-    k_hd_tc<<<ntasks, NTHREADS, smem, st>>>(map, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
-                                            band_gamma_tc(kp), band_coef_ff(ds_host.d), tc_stages(kp));
+    kern<<<ntasks, NTHREADS, smem, st>>>(map, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
+                                         band_gamma_tc(kp), band_coef_ff(ds_host.d), tc_stages(kp));
     return cudaGetLastError();
 }
 
