@@ -17,6 +17,7 @@ data exchange) and the slowest rank's time is reported.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -501,7 +502,19 @@ def run_c4(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / steps
 
+    # the same requests with halfspace depth on the tensor cores (split-BF16x3; exact counts)
+    reqs_tc = []
+    for q in reqs:
+        c = rrs.rrs_request()
+        ctypes.pointer(c)[0] = q
+        if c.kind == rrs.RRS_HALFSPACE and keep[len(reqs_tc)][3].d + 2 <= 128:
+            c.precision = rrs.RRS_PREC_SPLIT_BF16X3
+        reqs_tc.append(c)
+
     def batched():
+        rrs.rrs_depth_batched(ctx, reqs_tc, use_graph=True, stream=stream)
+
+    def batched_fp32():
         rrs.rrs_depth_batched(ctx, reqs, use_graph=True, stream=stream)
 
     def one_by_one():
@@ -519,19 +532,27 @@ def run_c4(args):
     launches = rrs.rrs_launch_count(ctx) - launches0
     clocks = sampler.stop()
     res_b = [out.cpu().numpy().copy() for _, _, out, _ in keep]
+    for _ in range(2):
+        batched_fp32()
+    ms_f = timed(batched_fp32, args.steps)
+    res_f = [out.cpu().numpy().copy() for _, _, out, _ in keep]
     one_by_one()
     torch.cuda.synchronize()
     ms_s = timed(one_by_one, max(1, args.steps // 2))
     rrs.rrs_check(ctx, stream)
-    same = all(np.array_equal(res_b[i], keep[i][2].cpu().numpy()) for i in range(len(keep)))
+    same = all(np.array_equal(res_b[i], keep[i][2].cpu().numpy()) and np.array_equal(res_f[i], res_b[i])
+               for i in range(len(keep)))
     line = {"metric": METRIC, "value": total_q / (ms_b / 1000), "unit": "query-depths/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_b, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32 (halfspace), f32 (projection)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_C4, "datasets": len(problems), "queries": total_q, "scale": args.scale,
                        "l2": "flushed between timed steps (512 MiB device write)"},
             "pd_per_s": pd_total / (ms_b / 1000), "gpu_launches": int(launches),
-            "one_call_per_request": {"ms_per_step": ms_s, "value": total_q / (ms_s / 1000)},
-            "speedup_batched_over_per_request": ms_s / ms_b, "results_identical": bool(same), "clocks": clocks}
+            "batched_fp32": {"ms_per_step": ms_f, "value": total_q / (ms_f / 1000)},
+            "one_call_per_request_fp32": {"ms_per_step": ms_s, "value": total_q / (ms_s / 1000)},
+            "speedup_batched_over_per_request": ms_s / ms_b, "speedup_tensor_cores_in_batch": ms_f / ms_b,
+            "results_identical": bool(same), "clocks": clocks}
     for did, _, _, _ in keep:
         rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
@@ -569,17 +590,25 @@ def run_c5(args):
     max_slots = 16384
     backlog_limit = 2 * max_slots
 
-    # warm the kernels
-    w = rrs.rrs_server_create(ctx, 256, 100, 100, stream)
-    tmp = np.zeros(4)
-    rid = rrs.rrs_server_submit(w, ids[0], reqs[0].Z[:4], 4, rrs.RRS_F32, 1, k, r, alpha, 0, tmp)
-    while not rrs.rrs_server_poll(w, rid):
+    # halfspace requests are served on the tensor cores (split-BF16x3, exact counts); the
+    # per-request arm is the plain FP32 path
+    tc = rrs.RRS_PREC_SPLIT_BF16X3
+    # warm the kernels (and build every dataset's BF16 planes before the clock starts)
+    w = rrs.rrs_server_create(ctx, 256, 100, 100, stream, precision=tc)
+    wids = []
+    for kind in (0, 1, 2):
+        for di in range(len(ids)):
+            if kind and di:
+                break
+            Zw = np.ascontiguousarray(datasets[di][:2])
+            wids.append(rrs.rrs_server_submit(w, ids[di], Zw, 2, rrs.RRS_F32, kind, k, r, alpha, 0, np.zeros(2)))
+    while not all(rrs.rrs_server_poll(w, rid) for rid in wids):
         rrs.rrs_server_step(w)
     rrs.rrs_server_destroy(w)
     torch.cuda.synchronize()
 
     # ---- continuous batching ----------------------------------------------------------------
-    srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream)
+    srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream, precision=tc)
     outs, lat, shed, served_q = {}, [], 0, 0
     inflight = collections.deque()
     backlog = 0
@@ -659,11 +688,11 @@ def run_c5(args):
     rrs.rrs_destroy(ctx)
     line = {"metric": METRIC, "value": cb["value"], "unit": "query-depths/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1000 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "bf16x3->f32 (halfspace), f32 (projection)", "data": "synthetic",
             "config": {"workload": WORKLOAD_C5, "rate_req_per_s": args.rate, "window_s": args.window,
                        "requests_offered": len(reqs), "scale": args.scale, "slots": max_slots,
                        "backlog_limit_queries": backlog_limit},
-            "continuous_batching": cb, "one_call_per_request": pr, "clocks": clocks}
+            "continuous_batching": cb, "one_call_per_request_fp32": pr, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

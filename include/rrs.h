@@ -143,6 +143,8 @@ typedef struct rrs_request {
     int64_t* count_out;        /* optional */
     int32_t* best_out;         /* optional */
     int32_t* round_choice_out; /* optional */
+    int32_t precision;         /* RRS_PREC_* (halfspace requests; 0 = FP32 CUDA cores) */
+    int32_t reserved;          /* set to 0 */
 } rrs_request;
 
 /*
@@ -151,7 +153,10 @@ typedef struct rrs_request {
  * request is served by one launch per pipeline stage over all requests
  * (Sec. 4: directions are independent within a round, queries are
  * independent).  Results are identical to calling rrs_depth on each request
- * alone with RRS_PREC_FP32_SIMT.  Requests may have different r; a request
+ * alone with the request's precision.  Halfspace requests with
+ * RRS_PREC_SPLIT_BF16X3 run on the tensor cores, one launch per dataset and
+ * round covering all of that dataset's such requests; their counts equal the
+ * FP32 path's (both are exact).  Requests may have different r; a request
  * leaves the batch when its rounds are done.
  *   reqs: host array of n_requests descriptors; all pointers inside are
  *   device pointers.  use_graph != 0 captures the launch sequence into a
@@ -257,20 +262,23 @@ rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out)
  * caller's host buffer.  Requests that arrive while others are on the GPU thus
  * join the next step's launches.  Every query keeps its own direction stream
  * (counter q = its row in its request) and state, so a request's depths do not
- * depend on what else is being served: they equal rrs_depth's FP32 results on
- * that request alone.
+ * depend on what else is being served: they equal rrs_depth's results on
+ * that request alone (at the server's precision).
  */
 typedef struct rrs_server rrs_server;
 
 /*
  * rrs_server_create - a server on ctx with max_slots query slots, each able to
  * hold a request of up to max_dirs_per_round directions per round (m) and
- * dimension max_d.  Device memory for the pool is taken once (counted against
- * the context's budget).  stream: cudaStream_t every server operation is
- * ordered on (NULL = legacy default stream).  Errors: INVALID_ARG, BUDGET, CUDA.
+ * dimension max_d.  precision: RRS_PREC_FP32_SIMT, or RRS_PREC_SPLIT_BF16X3 to
+ * serve halfspace requests on the tensor cores (datasets with d + 2 <= 128;
+ * others stay on the FP32 kernel; counts are exact either way).  Device memory
+ * for the pool is taken once (counted against the context's budget).  stream:
+ * cudaStream_t every server operation is ordered on (NULL = legacy default
+ * stream).  Errors: INVALID_ARG, BUDGET, CUDA.
  */
 rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_per_round, int32_t max_d,
-                             void* stream, rrs_server** out);
+                             int32_t precision, void* stream, rrs_server** out);
 
 /*
  * rrs_server_submit - queue a request: queries Z (host, n_queries x d, dtype)

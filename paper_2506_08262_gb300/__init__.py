@@ -58,6 +58,8 @@ class rrs_request(ctypes.Structure):
         ("count_out", ctypes.c_void_p),
         ("best_out", ctypes.c_void_p),
         ("round_choice_out", ctypes.c_void_p),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -90,8 +92,8 @@ _SIGS = {
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
     "rrs_profile_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
-    "rrs_server_create": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
-                           ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_create": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_server_submit": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
                            ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
@@ -220,10 +222,11 @@ def rrs_depth_noalloc(X, n: int, d: int, dtype: int, Z, n_queries: int, kind: in
            "rrs_depth_noalloc")
 
 
-def rrs_server_create(ctx: int, max_slots: int, max_dirs_per_round: int, max_d: int, stream=None) -> int:
+def rrs_server_create(ctx: int, max_slots: int, max_dirs_per_round: int, max_d: int, stream=None,
+                      precision: int = RRS_PREC_FP32_SIMT) -> int:
     h = ctypes.c_void_p()
-    _check(load().rrs_server_create(ctx, max_slots, max_dirs_per_round, max_d, _stream(stream), ctypes.byref(h)),
-           "rrs_server_create")
+    _check(load().rrs_server_create(ctx, max_slots, max_dirs_per_round, max_d, precision, _stream(stream),
+                                    ctypes.byref(h)), "rrs_server_create")
     return h.value
 
 

@@ -149,8 +149,14 @@ struct Plan {
     int rmax = 0;
     int max_ldx = 4;
     int64_t tot_ldx = 0, tot_d = 0, tot_u = 0, tot_m = 0;
-    bool any_tc = false;
-    int precision = RRS_PREC_FP32_SIMT;
+    // tensor-core halfspace tasks, one group per dataset (one tensor map per launch)
+    struct TcGroup {
+        int ds = 0;
+        std::vector<TaskDev> tasks;
+        std::vector<int> n;   // active prefix per round
+        TaskDev* d = nullptr;
+    };
+    std::vector<TcGroup> tc;
     // selection-kernel group size: autotuned choices and an explicit override (tuning probes)
     const std::map<std::tuple<int64_t, int, int>, int>* tune = nullptr;
     int force_group = 0;
@@ -180,6 +186,7 @@ struct ReqView {
     int32_t* best_out;
     int32_t* choice_out;
     int64_t q_base;
+    int32_t precision;   // RRS_PREC_* for halfspace requests
 };
 
 rrs_status validate_params(int32_t kind, int32_t k, int32_t r, double alpha, int32_t dtype, int32_t precision)
@@ -196,9 +203,8 @@ rrs_status validate_params(int32_t kind, int32_t k, int32_t r, double alpha, int
 }
 
 // Build the launch plan for a set of requests (requests sorted by r, descending).
-rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
+rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
 {
-    P.precision = precision;
     std::vector<int> order(reqs.size());
     for (size_t i = 0; i < reqs.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return reqs[a].r > reqs[b].r; });
@@ -248,7 +254,8 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
         const int m = (R.k + R.r - 1) / R.r;
         int G = 0;
         int cls = -1;
-        if (R.kind == RRS_HALFSPACE && precision == RRS_PREC_FP32_SIMT && D.ldx > 440)
+        const bool tc = R.kind == RRS_HALFSPACE && R.precision == RRS_PREC_SPLIT_BF16X3;
+        if (R.kind == RRS_HALFSPACE && !tc && D.ldx > 440)
             return fail(RRS_ERR_UNSUPPORTED, "FP32 halfspace kernel stages 128 rows of d floats; d=%d too large", D.d);
         if (R.kind != RRS_HALFSPACE) {
             if (D.n > 0x7FFFFFFF) return fail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
@@ -303,7 +310,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             P.max_ldx = std::max(P.max_ldx, D.ldx);
             for (int j0 = 0; j0 < m; j0 += 128) P.gen_tasks.push_back(TaskDev{s, j0, std::min(128, m - j0), 0});
             if (R.kind == RRS_HALFSPACE) {
-                if (precision != RRS_PREC_SPLIT_BF16X3) {
+                if (!tc) {
                     const int cap = 64;   // directions per CTA of the FP32 kernel
                     const int nt = (m + cap - 1) / cap;
                     const int per = (m + nt - 1) / nt;
@@ -314,13 +321,21 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
             }
             P.argmin_list.push_back(s);
         }
-        if (R.kind == RRS_HALFSPACE && precision == RRS_PREC_SPLIT_BF16X3) {
+        if (tc) {
             // tensor-core tasks: 128 consecutive (query, direction) rows of this request, so the
             // accumulator's M dimension is filled across queries (task = first query slot, offset
-            // into that query's directions, row count)
+            // into that query's directions, row count); one task list per dataset
+            const int dsi = dsidx[R.dset];
+            size_t gi = 0;
+            while (gi < P.tc.size() && P.tc[gi].ds != dsi) ++gi;
+            if (gi == P.tc.size()) {
+                P.tc.emplace_back();
+                P.tc.back().ds = dsi;
+            }
             const int64_t rows = R.nq * (int64_t)m;
             for (int64_t g = 0; g < rows; g += 128)
-                P.hd_tasks.push_back(TaskDev{s_first + (int)(g / m), (int)(g % m), (int)std::min<int64_t>(128, rows - g), 0});
+                P.tc[gi].tasks.push_back(
+                    TaskDev{s_first + (int)(g / m), (int)(g % m), (int)std::min<int64_t>(128, rows - g), 0});
         }
         P.rmax = std::max(P.rmax, R.r);
     }
@@ -335,6 +350,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, int precision, Plan& P)
     };
     prefix(P.gen_tasks, P.n_gen);
     prefix(P.hd_tasks, P.n_hd);
+    for (auto& g : P.tc) prefix(g.tasks, g.n);
     P.n_pd.resize(P.pd_tasks.size());
     for (size_t c = 0; c < P.pd_tasks.size(); ++c) prefix(P.pd_tasks[c], P.n_pd[c]);
     P.n_arg.assign(P.rmax, 0);
@@ -352,6 +368,7 @@ size_t carve_plan(Plan& P, Carve& C)
     P.d_slots = C.take<SlotDev>(P.slots.size());
     P.d_gen = C.take<TaskDev>(P.gen_tasks.size());
     P.d_hd = C.take<TaskDev>(P.hd_tasks.size());
+    for (auto& g : P.tc) g.d = C.take<TaskDev>(g.tasks.size());
     P.d_pd.resize(P.pd_tasks.size());
     for (size_t c = 0; c < P.pd_tasks.size(); ++c) P.d_pd[c] = C.take<TaskDev>(P.pd_tasks[c].size());
     P.d_arg = C.take<int32_t>(P.argmin_list.size());
@@ -376,6 +393,7 @@ rrs_status upload_plan(rrs_ctx* ctx, Plan& P, cudaStream_t st)
     CUDA_TRY(up(P.d_slots, P.slots.data(), P.slots.size() * sizeof(SlotDev)));
     CUDA_TRY(up(P.d_gen, P.gen_tasks.data(), P.gen_tasks.size() * sizeof(TaskDev)));
     CUDA_TRY(up(P.d_hd, P.hd_tasks.data(), P.hd_tasks.size() * sizeof(TaskDev)));
+    for (auto& g : P.tc) CUDA_TRY(up(g.d, g.tasks.data(), g.tasks.size() * sizeof(TaskDev)));
     for (size_t c = 0; c < P.pd_tasks.size(); ++c)
         CUDA_TRY(up(P.d_pd[c], P.pd_tasks[c].data(), P.pd_tasks[c].size() * sizeof(TaskDev)));
     CUDA_TRY(up(P.d_arg, P.argmin_list.data(), P.argmin_list.size() * sizeof(int32_t)));
@@ -402,17 +420,18 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
             ctx->stage_launches[RRS_STAGE_GEN]++;
         }
         if (P.n_hd[l] > 0) {
-            if (P.precision == RRS_PREC_SPLIT_BF16X3) {
-                StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
-                CUDA_TRY(launch_hd_tc(P.d_hd, P.n_hd[l], P.d_slots, P.d_ds, P.ds[0], P.U, P.yz, P.z64, P.res,
-                                      nullptr, ctx->d_err, st));
-                ctx->stage_launches[RRS_STAGE_HD_TC]++;
-            } else {
-                StageTimer t(ctx, RRS_STAGE_HD_SIMT, st, capturing);
-                CUDA_TRY(launch_hd_simt(P.d_hd, P.n_hd[l], P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res,
-                                        nullptr, ctx->d_err, st));
-                ctx->stage_launches[RRS_STAGE_HD_SIMT]++;
-            }
+            StageTimer t(ctx, RRS_STAGE_HD_SIMT, st, capturing);
+            CUDA_TRY(launch_hd_simt(P.d_hd, P.n_hd[l], P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz, P.z64, P.res,
+                                    nullptr, ctx->d_err, st));
+            ctx->stage_launches[RRS_STAGE_HD_SIMT]++;
+            ctx->launches++;
+        }
+        for (auto& g : P.tc) {
+            if (g.n[l] <= 0) continue;
+            StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
+            CUDA_TRY(launch_hd_tc(g.d, g.n[l], P.d_slots, P.d_ds, P.ds[g.ds], P.U, P.yz, P.z64, P.res, nullptr,
+                                  ctx->d_err, st));
+            ctx->stage_launches[RRS_STAGE_HD_TC]++;
             ctx->launches++;
         }
         for (size_t c = 0; c < P.pd_tasks.size(); ++c) {
@@ -599,7 +618,7 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id)
 }  // extern "C"
 
 // Lazily build the BF16 planes of a dataset for the tensor-core path.
-static rrs_status ensure_bf16_planes(rrs_ctx* ctx, Dataset& D)
+rrs_status rrs::ensure_bf16_planes(rrs_ctx* ctx, Dataset& D)
 {
     if (D.Xbf) return RRS_OK;
     if (!hd_tc_supported(D.d)) return fail(RRS_ERR_UNSUPPORTED, "tensor-core path does not support d=%d", D.d);
@@ -616,13 +635,12 @@ static rrs_status ensure_bf16_planes(rrs_ctx* ctx, Dataset& D)
     return RRS_OK;
 }
 
-static rrs_status run_requests(rrs_ctx* ctx, std::vector<ReqView>& reqs, int precision, cudaStream_t st,
-                               int force_group = 0)
+static rrs_status run_requests(rrs_ctx* ctx, std::vector<ReqView>& reqs, cudaStream_t st, int force_group = 0)
 {
     Plan P;
     P.tune = &ctx->pd_tune;
     P.force_group = force_group;
-    rrs_status s = build_plan(reqs, precision, P);
+    rrs_status s = build_plan(reqs, P);
     if (s != RRS_OK) return s;
     if (P.slots.empty()) return RRS_OK;
     Carve sizing;
@@ -691,6 +709,7 @@ rrs_status rrs_depth(rrs_ctx* ctx, int64_t dataset_id, const void* Z, int64_t n_
     R.alpha = (float)cap_shrink;
     R.seed = seed;
     R.q_base = 0;
+    R.precision = precision;
     if (out_on_device) {
         R.depth_out = depth_out;
         R.count_out = count_out;
@@ -715,7 +734,7 @@ rrs_status rrs_depth(rrs_ctx* ctx, int64_t dataset_id, const void* Z, int64_t n_
         return fail(RRS_ERR_INVALID_ARG, "Z holds a non-finite value or one of magnitude >= 2^64");
     }
     std::vector<ReqView> reqs{R};
-    s = run_requests(ctx, reqs, precision, st);
+    s = run_requests(ctx, reqs, st);
     if (s == RRS_OK && !out_on_device) {
         CUDA_TRY(cudaMemcpyAsync(depth_out, R.depth_out, ob_depth, cudaMemcpyDeviceToHost, st));
         if (count_out) CUDA_TRY(cudaMemcpyAsync(count_out, R.count_out, ob_count, cudaMemcpyDeviceToHost, st));
@@ -739,16 +758,24 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
     std::vector<ReqView> views;
     for (int i = 0; i < n_requests; ++i) {
         const rrs_request& q = reqs[i];
-        rrs_status s = validate_params(q.kind, q.n_dirs, q.n_refinements, q.cap_shrink, q.dtype, RRS_PREC_FP32_SIMT);
-        if (s != RRS_OK) return s;
+        rrs_status s = validate_params(q.kind, q.n_dirs, q.n_refinements, q.cap_shrink, q.dtype, q.precision);
+        if (s != RRS_OK) {
+            const std::string why = rrs_last_error();
+            return fail(s, "request %d: %s", i, why.c_str());
+        }
         if (q.n_queries < 0 || (q.n_queries > 0 && (!q.Z || !q.depth_out)))
             return fail(RRS_ERR_INVALID_ARG, "request %d: bad query batch or outputs", i);
         auto it = ctx->datasets.find(q.dataset_id);
         if (it == ctx->datasets.end()) return fail(RRS_ERR_NOT_FOUND, "request %d: no dataset %lld", i,
                                                    (long long)q.dataset_id);
         if (q.n_queries == 0) continue;
+        if (q.precision == RRS_PREC_SPLIT_BF16X3) {
+            s = ensure_bf16_planes(ctx, it->second);
+            if (s != RRS_OK) return s;
+        }
         ReqView R{};
         R.dset = &it->second;
+        R.precision = q.precision;
         R.Z = q.Z;
         R.nq = q.n_queries;
         R.dtype = q.dtype;
@@ -765,7 +792,7 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
         views.push_back(R);
     }
     if (views.empty()) return RRS_OK;
-    if (!use_graph) return run_requests(ctx, views, RRS_PREC_FP32_SIMT, st);
+    if (!use_graph) return run_requests(ctx, views, st);
 
     // graph path: identical descriptors replay a captured launch sequence
     std::vector<char> key((const char*)reqs, (const char*)reqs + sizeof(rrs_request) * n_requests);
@@ -778,7 +805,7 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
     }
     Plan P;
     P.tune = &ctx->pd_tune;
-    rrs_status s = build_plan(views, RRS_PREC_FP32_SIMT, P);
+    rrs_status s = build_plan(views, P);
     if (s != RRS_OK) return s;
     Carve sizing;
     const size_t bytes = carve_plan(P, sizing);
@@ -870,9 +897,10 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
     R.k = m;
     R.r = 1;
     R.alpha = 0.5f;
+    R.precision = precision;
     std::vector<ReqView> reqs{R};
     Plan P;
-    s = build_plan(reqs, precision, P);
+    s = build_plan(reqs, P);
     if (s != RRS_OK) return s;
     Carve sizing;
     const size_t bytes = carve_plan(P, sizing) + sizeof(int64_t) * n_queries + 512;
@@ -896,8 +924,8 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
         trace("debug_round_depths: y_z done");
         if (kind == RRS_HALFSPACE) {
             if (precision == RRS_PREC_SPLIT_BF16X3)
-                CUDA_TRY(launch_hd_tc(P.d_hd, (int)P.hd_tasks.size(), P.d_slots, P.d_ds, P.ds[0], P.U, P.yz, P.z64,
-                                      P.res, band, ctx->d_err, st));
+                CUDA_TRY(launch_hd_tc(P.tc[0].d, (int)P.tc[0].tasks.size(), P.d_slots, P.d_ds, P.ds[0], P.U, P.yz,
+                                      P.z64, P.res, band, ctx->d_err, st));
             else
                 CUDA_TRY(launch_hd_simt(P.d_hd, (int)P.hd_tasks.size(), P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz,
                                         P.z64, P.res, band, ctx->d_err, st));
@@ -996,7 +1024,7 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
         for (int rep = 0; rep < 3; ++rep) {
             std::vector<ReqView> reqs{R};
             CUDA_TRY(cudaEventRecord(a, 0));
-            s = run_requests(ctx, reqs, RRS_PREC_FP32_SIMT, 0, G);
+            s = run_requests(ctx, reqs, 0, G);
             if (s != RRS_OK) break;
             CUDA_TRY(cudaEventRecord(b, 0));
             CUDA_TRY(cudaEventSynchronize(b));

@@ -62,3 +62,9 @@ struct rrs_ctx {
     double stage_ms[RRS_NSTAGES] = {};
     int64_t stage_launches[RRS_NSTAGES] = {};
 };
+
+namespace rrs {
+// Build (once) the BF16 hi/lo planes the tensor-core halfspace kernel streams;
+// UNSUPPORTED for d + 2 > 128, BUDGET when they do not fit the context's budget.
+rrs_status ensure_bf16_planes(rrs_ctx* ctx, Dataset& D);
+}  // namespace rrs

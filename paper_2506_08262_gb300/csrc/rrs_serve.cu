@@ -100,6 +100,7 @@ struct rrs_server {
     rrs_ctx* ctx = nullptr;
     cudaStream_t st = nullptr;
     int cap = 0, max_m = 0, max_d = 0, max_ldx = 0;
+    int precision = RRS_PREC_FP32_SIMT;   // halfspace arithmetic (tensor cores where the dataset allows)
     // device arena
     void* arena = nullptr;
     size_t arena_bytes = 0;
@@ -141,7 +142,11 @@ rrs_status ensure_dataset(rrs_server* S, int64_t id, int* row)
     auto it = S->ctx->datasets.find(id);
     if (it == S->ctx->datasets.end()) return sfail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)id);
     if ((int)S->ds_host.size() >= S->ds_cap) return sfail(RRS_ERR_BUDGET, "server dataset table full");
-    const Dataset& D = it->second;
+    Dataset& D = it->second;
+    if (S->precision == RRS_PREC_SPLIT_BF16X3 && hd_tc_supported(D.d)) {
+        const rrs_status s = ensure_bf16_planes(S->ctx, D);
+        if (s != RRS_OK) return s;
+    }
     DsDev dd{};
     dd.X32 = D.X32;
     dd.X64 = D.X64;
@@ -237,9 +242,10 @@ rrs_status admit(rrs_server* S)
 extern "C" {
 
 rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_per_round, int32_t max_d,
-                             void* stream, rrs_server** out)
+                             int32_t precision, void* stream, rrs_server** out)
 {
-    if (!ctx || !out || max_slots < 1 || max_dirs_per_round < 1 || max_d < 1 || max_d > 1024)
+    if (!ctx || !out || max_slots < 1 || max_dirs_per_round < 1 || max_d < 1 || max_d > 1024 ||
+        (precision != RRS_PREC_FP32_SIMT && precision != RRS_PREC_SPLIT_BF16X3))
         return sfail(RRS_ERR_INVALID_ARG, "bad server parameters");
     *out = nullptr;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -251,6 +257,7 @@ rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_p
     S->max_m = max_dirs_per_round;
     S->max_d = max_d;
     S->max_ldx = padded(max_d);
+    S->precision = precision;
     S->ds_cap = 4096;
     const size_t c = (size_t)max_slots;
     size_t off = 0;
@@ -337,6 +344,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
     if (!S->active.empty()) {
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
+        std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
         std::map<std::tuple<size_t, int, int>, std::vector<TaskDev>> pd;
         std::vector<int32_t> arg;
         const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
@@ -354,9 +362,15 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                     }
             }
             const int hper = (R->m + ((R->m + 63) / 64) - 1) / ((R->m + 63) / 64);
+            const int row = S->ds_index[R->dataset];
+            const bool use_tc = R->kind == RRS_HALFSPACE && S->precision == RRS_PREC_SPLIT_BF16X3 && D.kp > 0;
             for (int32_t slot : R->slots) {
                 for (int j0 = 0; j0 < R->m; j0 += 128) gen.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
-                if (R->kind == RRS_HALFSPACE) {
+                if (use_tc) {
+                    // slots of a request need not be adjacent: one task never crosses a slot
+                    auto& v = tc[row];
+                    for (int j0 = 0; j0 < R->m; j0 += 128) v.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
+                } else if (R->kind == RRS_HALFSPACE) {
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
                 } else {
                     auto& v = pd[std::make_tuple(cls, G, pdap_dp4_class(D.d))];
@@ -366,6 +380,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             }
         }
         size_t need = sizeof(TaskDev) * (gen.size() + hd.size()) + sizeof(int32_t) * arg.size() + 1024;
+        for (auto& kv : tc) need += sizeof(TaskDev) * kv.second.size() + 256;
         for (auto& kv : pd) need += sizeof(TaskDev) * kv.second.size() + 256;
         s = step_table(S, need);
         if (s != RRS_OK) return s;
@@ -382,12 +397,18 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         const size_t o_arg = put(arg.data(), sizeof(int32_t) * arg.size());
         std::vector<std::pair<size_t, std::tuple<size_t, int, int>>> o_pd;
         for (auto& kv : pd) o_pd.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
+        std::vector<std::pair<size_t, int>> o_tc;
+        for (auto& kv : tc) o_tc.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
         S_TRY(cudaMemcpyAsync(S->d_tab, host.data(), off, cudaMemcpyHostToDevice, S->st));
         char* T = S->d_tab;
         S_TRY(launch_gen_slotround((const TaskDev*)(T + o_gen), (int)gen.size(), S->d_slots, S->d_p0, S->d_p1,
                                    S->d_z64, S->d_U, S->d_yz, S->st));
         S_TRY(launch_hd_simt((const TaskDev*)(T + o_hd), (int)hd.size(), S->max_ldx, S->d_slots, S->d_ds, S->d_U,
                              S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err, S->st));
+        for (auto& to : o_tc)
+            S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), S->d_slots, S->d_ds,
+                               S->ds_host[to.second], S->d_U, S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err,
+                               S->st));
         for (auto& po : o_pd) {
             const auto& key = po.second;
             S_TRY(launch_pdap((const TaskDev*)(T + po.first), (int)pd[key].size(), std::get<0>(key), std::get<1>(key),
@@ -396,7 +417,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         }
         S_TRY(launch_argmin_slotround(S->d_slots, (const int32_t*)(T + o_arg), (int)arg.size(), S->d_U, S->d_res,
                                      S->d_p0, S->d_p1, S->st));
-        S->ctx->launches += 3 + pd.size();
+        S->ctx->launches += 3 + pd.size() + tc.size();
         // retire requests whose last round just ran
         std::vector<Request*> still;
         for (Request* R : S->active) {

@@ -106,3 +106,46 @@ def test_batched_rejects_bad_request(ctx):
         rrs.rrs_depth_batched(ctx.handle, [bad])
     assert e.value.status == rrs.RRS_ERR_INVALID_ARG
     ctx.free(did)
+
+
+def test_batched_tensor_core_halfspace(ctx):
+    # halfspace requests on the tensor cores inside a mixed batch (datasets of uneven n and d,
+    # d on both sides of the 64-wide K extent): results equal rrs_depth alone at the same
+    # precision, and the counts equal the FP32 path's
+    problems = workloads.c4(seed=47, n_datasets=8, n_lo=100, n_hi=3000, q_hi=12, scale=1.0)
+    for i, P in enumerate(problems):
+        P.k, P.r = 150, 3
+        P.kind = 0 if i % 3 != 2 else 1
+    reqs, outs, ids = make_requests(ctx, problems)
+    for i, P in enumerate(problems):
+        if P.kind == 0:
+            reqs[i].precision = rrs.RRS_PREC_SPLIT_BF16X3
+    for use_graph in (False, True):
+        rrs.rrs_depth_batched(ctx.handle, reqs, use_graph=use_graph, stream=torch.cuda.current_stream())
+        rrs.rrs_check(ctx.handle, torch.cuda.current_stream())
+        for i, P in enumerate(problems):
+            prec = reqs[i].precision
+            dep, cnt, best, ch = ctx.depth(ids[i], outs[i]["Z"], P.kind, P.k, P.r, P.alpha, P.seed + i,
+                                           precision=prec, rounds=True)
+            np.testing.assert_array_equal(outs[i]["depth"].cpu().numpy(), dep.cpu().numpy())
+            np.testing.assert_array_equal(outs[i]["choice"].cpu().numpy(), ch.cpu().numpy())
+            if P.kind == 0:
+                np.testing.assert_array_equal(outs[i]["count"].cpu().numpy(), cnt.cpu().numpy())
+                d32, c32, _, _ = ctx.depth(ids[i], outs[i]["Z"], 0, P.k, P.r, P.alpha, P.seed + i, rounds=True)
+                np.testing.assert_array_equal(outs[i]["count"].cpu().numpy(), c32.cpu().numpy())
+    for did in ids:
+        ctx.free(did)
+
+
+def test_batched_rejects_tensor_cores_for_projection_depth(ctx):
+    X = torch.zeros((5, 3), dtype=torch.float32, device="cuda")
+    did = ctx.register(X)
+    Z = torch.zeros((2, 3), dtype=torch.float32, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    bad = rrs.rrs_request(dataset_id=did, Z=Z.data_ptr(), n_queries=2, dtype=rrs.RRS_F32, kind=1, n_dirs=4,
+                          n_refinements=2, cap_shrink=0.5, seed=0, depth_out=out.data_ptr(),
+                          precision=rrs.RRS_PREC_SPLIT_BF16X3)
+    with pytest.raises(rrs.RRSError) as e:
+        rrs.rrs_depth_batched(ctx.handle, [bad])
+    assert e.value.status == rrs.RRS_ERR_INVALID_ARG
+    ctx.free(did)

@@ -36,9 +36,10 @@ def setup():
 K, R, ALPHA = 120, 4, 0.8
 
 
-def serve(ctx, batches, max_slots=4096):
+def serve(ctx, batches, max_slots=4096, precision=rrs.RRS_PREC_FP32_SIMT):
     """batches: list (one per step) of lists of (dataset_id, Z, kind, seed) to submit before that step."""
-    srv = rrs.rrs_server_create(ctx.handle, max_slots, -(-K // R), 100, torch.cuda.current_stream())
+    srv = rrs.rrs_server_create(ctx.handle, max_slots, -(-K // R), 100, torch.cuda.current_stream(),
+                                precision=precision)
     results, pending = [], {}
     try:
         step = 0
@@ -62,8 +63,9 @@ def serve(ctx, batches, max_slots=4096):
     return results
 
 
-def alone_depth(ctx, did, Z, kind, seed):
-    dep, _, _ = ctx.depth(did, torch.from_numpy(Z).cuda(), kind, K, R, ALPHA, seed)
+def alone_depth(ctx, did, Z, kind, seed, precision=rrs.RRS_PREC_FP32_SIMT):
+    prec = precision if kind == 0 else rrs.RRS_PREC_FP32_SIMT
+    dep, _, _ = ctx.depth(did, torch.from_numpy(Z).cuda(), kind, K, R, ALPHA, seed, precision=prec)
     return dep.cpu().numpy()
 
 
@@ -120,3 +122,21 @@ def test_oversize_request_is_rejected(setup):
         assert e.value.status == rrs.RRS_ERR_UNSUPPORTED
     finally:
         rrs.rrs_server_destroy(srv)
+
+
+def test_tensor_core_server_same_alone_and_in_the_mix(setup):
+    # halfspace requests served on the tensor cores: each result equals rrs_depth alone at the
+    # same precision, and (counts being exact) the FP32 server's result
+    ctx, ds = setup
+    TCP = rrs.RRS_PREC_SPLIT_BF16X3
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(9):
+        did, P = ds[i % len(ds)]
+        q = int(rng.integers(1, min(P.nq, 25) + 1))
+        reqs.append((did, np.ascontiguousarray(P.Z[:q]), 0 if i % 3 else 1 + (i % 2), 300 + i))
+    mix = serve(ctx, [reqs[:3], reqs[3:5], reqs[5:]], precision=TCP)
+    fp32 = serve(ctx, [reqs[:3], reqs[3:5], reqs[5:]])
+    for (did, Z, kind, seed), got, ref32 in zip(reqs, mix, fp32):
+        np.testing.assert_array_equal(got, alone_depth(ctx, did, Z, kind, seed, precision=TCP))
+        np.testing.assert_array_equal(got, ref32)
