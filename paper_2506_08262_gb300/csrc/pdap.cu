@@ -3,19 +3,20 @@
 // MAD_+) of the FP32 keys, depth in FP64 from those few values.
 //
 // One CTA handles G <= 4 directions of one query with the G*n keys resident in
-// shared memory.  Selection is bucket based and exact:
-//   pass A  project every point on the G directions, store the keys and add
-//           each to a 2048-bucket histogram over [-R, R], R = max |x_i| (a bound
-//           on every |u'x_i|), bucket = monotone FP32 map of the key;
-//   pass C  gather the keys of the buckets holding the median ranks (and,
-//           for D_AP, of the buckets expected to hold the MAD_+ ranks), then
+// shared memory.  The whole CTA projects (pass A: every point on the G
+// directions, keys stored, each added to a 2048-bucket histogram over
+// u'c +- 5 sigma_u, bucket = monotone FP32 map of the key).  Then the CTA
+// splits into G groups of NT/G threads, one per direction, each synchronising
+// on its own named barrier, so the directions never wait for one another:
+//   median  find the buckets of the median ranks, gather their keys (and, for
+//           D_AP, the keys of the buckets expected to hold the MAD_+ ranks),
 //           rank them exactly;
-//   D_P     histogram of |y - med| over [0, R + |med|], gather, rank (MAD).
+//   D_P     histogram of |y - med|, gather the MAD buckets, rank (MAD).
 // Bucket maps are monotone, so every bucket holds a contiguous run of ranks
-// and the gathered keys contain the wanted order statistics.  When a bucket
-// run holds more keys than the gather buffer, or the D_AP guess of the
-// positive count was wrong, that direction falls back to an iterated bucket
-// selection over its keys.  No per-element work uses FP64.
+// and the gathered keys contain the wanted order statistics.  When a run holds
+// more keys than the gather buffer, or the D_AP guess of the positive count
+// was wrong, the group falls back to an iterated bucket selection over its
+// keys.  No per-element work uses FP64.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -32,27 +33,31 @@ constexpr int NB = 2048;     // buckets per direction
 constexpr int CAP = 256;     // gathered keys per direction and target
 constexpr int MAXG = 4;
 constexpr int FB_NB = NB;    // fallback histogram (reuses the bucket area)
-constexpr int FB_CAP = 512;  // fallback gather buffer (reuses the gather area; 2*CAP*G >= 512)
+constexpr int FB_CAP = 2 * CAP;  // fallback gather buffer: a direction's two gather areas
 
+// Per-direction constants and per-group scratch: after the projection pass,
+// group g (NT / G threads) works on direction g alone and synchronises with
+// the named barrier 1 + g, so the directions of a CTA never wait for each other.
 struct Ctl {
-    int b_lo[MAXG][2], b_hi[MAXG][2];  // bucket runs: [0] median (or MAD), [1] MAD_+ guess
-    int c_lo[MAXG][2];                 // keys below the run
-    int cnt[MAXG][2];                  // keys in the run
-    int fill[MAXG][2];                 // keys gathered so far
-    int fb[MAXG];                      // 1: fall back for all statistics, 2: only MAD_+
     float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: about (y - lo_b) * sc_y
     float off_y[MAXG];                 // -lo_b * sc_y (bucket_fma offset)
     float scale[MAXG];                 // sigma_u (or the radius) of each direction
-    float cen[MAXG], sc_d[MAXG];       // bucket map of |y - med| (D_P)
-    float v1[MAXG][2], v2[MAXG][2];    // selected order statistics
     float yz[MAXG];
-    int nle[MAXG];                     // #(y <= m1)
-    int npos[MAXG];                    // #(y > med), D_AP
-    int red[NWARP];
-    float fred[2 * NWARP];
-    // generic fallback
-    int g_b1, g_b2, g_c1, g_c2, g_n;
-    float g_v1, g_v2;
+    int red[MAXG][NWARP];
+    float fred[MAXG][2 * NWARP];
+    int fill[MAXG][2];
+    int f_b1[MAXG], f_c1[MAXG], f_b2[MAXG], f_c2[MAXG];   // bucket search results
+    float pv1[MAXG], pv2[MAXG];                           // rank pick results
+    int gn[MAXG];
+};
+
+template <int GS>
+struct Grp {
+    int g, t;   // direction (group) index, thread index within the group
+    __device__ __forceinline__ void sync() const
+    {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GS) : "memory");
+    }
 };
 
 __device__ __forceinline__ int bucket(float y, float lo, float scale)
@@ -83,17 +88,54 @@ __device__ __forceinline__ float warp_min(float v)
     return v;
 }
 
-// Exclusive scan of h[0..NB) by the whole CTA; records the bucket holding
-// rank ra and the one holding rank rb (ra <= rb), with the keys below each.
-__device__ void find_buckets(const unsigned* h, int ra, int rb, Ctl& C, int& ba, int& ca, int& bb, int& cb)
+// Group sum of one int per thread (every thread gets the total).
+template <int GS>
+__device__ int gsum(const Grp<GS>& q, int c, Ctl& C)
 {
-    constexpr int PER = NB / NT;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if ((q.t & 31) == 0) C.red[q.g][q.t >> 5] = c;
+    q.sync();
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < GS / 32; ++i) s += C.red[q.g][i];
+    q.sync();
+    return s;
+}
+
+// Group min and max.
+template <int GS>
+__device__ void gminmax(const Grp<GS>& q, float lo, float hi, Ctl& C, float& olo, float& ohi)
+{
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if ((q.t & 31) == 0) {
+        C.fred[q.g][q.t >> 5] = lo;
+        C.fred[q.g][NWARP + (q.t >> 5)] = hi;
+    }
+    q.sync();
+    olo = C.fred[q.g][0];
+    ohi = C.fred[q.g][NWARP];
+#pragma unroll
+    for (int i = 1; i < GS / 32; ++i) {
+        olo = fminf(olo, C.fred[q.g][i]);
+        ohi = fmaxf(ohi, C.fred[q.g][NWARP + i]);
+    }
+    q.sync();
+}
+
+// Exclusive scan of h[0..NB) by the group; the bucket holding rank ra and the
+// one holding rank rb (ra <= rb, both below the total), with the keys below each.
+template <int GS>
+__device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, Ctl& C, int& ba, int& ca, int& bb, int& cb)
+{
+    constexpr int PER = NB / GS;
+    const int lane = q.t & 31, w = q.t >> 5;
     int own = 0;
     unsigned v[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        v[k] = h[tid * PER + k];
+        v[k] = h[q.t * PER + k];
         own += (int)v[k];
     }
     int incl = own;
@@ -102,50 +144,62 @@ __device__ void find_buckets(const unsigned* h, int ra, int rb, Ctl& C, int& ba,
         const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += y;
     }
-    __syncthreads();
-    if (lane == 31) C.red[w] = incl;
-    __syncthreads();
+    if (lane == 31) C.red[q.g][w] = incl;
+    q.sync();
     int base = 0;
-    for (int i = 0; i < w; ++i) base += C.red[i];
+    for (int i = 0; i < w; ++i) base += C.red[q.g][i];
     int c = base + incl - own;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int hk = (int)v[k];
         if (hk > 0) {
-            if (c <= ra && ra < c + hk) { C.g_b1 = tid * PER + k; C.g_c1 = c; }
-            if (c <= rb && rb < c + hk) { C.g_b2 = tid * PER + k; C.g_c2 = c; }
+            if (c <= ra && ra < c + hk) {
+                C.f_b1[q.g] = q.t * PER + k;
+                C.f_c1[q.g] = c;
+            }
+            if (c <= rb && rb < c + hk) {
+                C.f_b2[q.g] = q.t * PER + k;
+                C.f_c2[q.g] = c;
+            }
         }
         c += hk;
     }
-    __syncthreads();
-    ba = C.g_b1;
-    ca = C.g_c1;
-    bb = C.g_b2;
-    cb = C.g_c2;
-    __syncthreads();
+    q.sync();
+    ba = C.f_b1[q.g];
+    ca = C.f_c1[q.g];
+    bb = C.f_b2[q.g];
+    cb = C.f_c2[q.g];
+    q.sync();
 }
 
-// Rank among buf[0..cnt): values of 0-based ranks s1 <= s2.
-__device__ __forceinline__ void rank_pick(const float* buf, int cnt, int t, int s1, int s2, float& o1, float& o2)
+// Values of the 0-based ranks s1 <= s2 among buf[0..cnt), by the group.
+template <int GS>
+__device__ void gpick(const Grp<GS>& q, const float* buf, int cnt, int s1, int s2, Ctl& C, float& o1, float& o2)
 {
-    const float v = buf[t];
-    int nlt = 0, nle = 0;
-    for (int s = 0; s < cnt; ++s) {
-        const float w2 = buf[s];
-        nlt += (w2 < v);
-        nle += (w2 <= v);
+    for (int t = q.t; t < cnt; t += GS) {
+        const float v = buf[t];
+        int nlt = 0, nle = 0;
+        for (int s = 0; s < cnt; ++s) {
+            const float w2 = buf[s];
+            nlt += (w2 < v);
+            nle += (w2 <= v);
+        }
+        if (nlt <= s1 && s1 < nle) C.pv1[q.g] = v;
+        if (nlt <= s2 && s2 < nle) C.pv2[q.g] = v;
     }
-    if (nlt <= s1 && s1 < nle) o1 = v;
-    if (nlt <= s2 && s2 < nle) o2 = v;
+    q.sync();
+    o1 = C.pv1[q.g];
+    o2 = C.pv2[q.g];
+    q.sync();
 }
 
-// Generic exact selection over one direction's keys f(0..L-1), all in
-// [lo, hi], by iterated bucketing (the fallback path).
-template <class F>
-__device__ void select_generic(F f, int L, int q1, int q2, float lo, float hi, unsigned* hist, float* buf, Ctl& C,
-                               float& v1, float& v2, int* err)
+// Generic exact selection of ranks q1 <= q2 over one direction's values f(0..L-1),
+// all in [lo, hi], by iterated bucketing (the fallback path); hist and buf are the
+// direction's own areas.
+template <int GS, class F>
+__device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, float hi, unsigned* hist, float* buf,
+                        Ctl& C, float& v1, float& v2, int* err)
 {
-    const int tid = threadIdx.x;
     int below = 0;
     for (int iter = 0; iter < 24; ++iter) {
         if (!(lo < hi)) {
@@ -154,46 +208,35 @@ __device__ void select_generic(F f, int L, int q1, int q2, float lo, float hi, u
         }
         float scale = __fdiv_rn((float)FB_NB, __fsub_rn(hi, lo));
         if (!(scale <= FLT_MAX)) scale = FLT_MAX;
-        for (int b = tid; b < FB_NB; b += NT) hist[b] = 0u;
-        __syncthreads();
-        for (int i = tid; i < L; i += NT) {
+        for (int b = q.t; b < FB_NB; b += GS) hist[b] = 0u;
+        q.sync();
+        for (int i = q.t; i < L; i += GS) {
             const float a = f(i);
             if (a >= lo && a <= hi) atomicAdd(&hist[bucket(a, lo, scale)], 1u);
         }
-        __syncthreads();
+        q.sync();
         int b1, c1, b2, c2;
-        find_buckets(hist, q1 - below, q2 - below, C, b1, c1, b2, c2);
+        gfind(q, hist, q1 - below, q2 - below, C, b1, c1, b2, c2);
         const int cnt = c2 + (int)hist[b2] - c1;
-        if (tid == 0) C.g_n = 0;
-        __syncthreads();
+        if (q.t == 0) C.gn[q.g] = 0;
+        q.sync();
         if (cnt <= FB_CAP) {
-            for (int i = tid; i < L; i += NT) {
+            for (int i = q.t; i < L; i += GS) {
                 const float a = f(i);
                 if (a >= lo && a <= hi) {
                     const int b = bucket(a, lo, scale);
                     if (b >= b1 && b <= b2) {
-                        const int pos = atomicAdd(&C.g_n, 1);
+                        const int pos = atomicAdd(&C.gn[q.g], 1);
                         if (pos < FB_CAP) buf[pos] = a;
                     }
                 }
             }
-            __syncthreads();
-            const int s1 = q1 - below - c1, s2 = q2 - below - c1;
-            float o1 = 0.f, o2 = 0.f;
-            for (int t = tid; t < cnt; t += NT) {
-                o1 = o2 = __int_as_float(0x7FC00000);
-                rank_pick(buf, cnt, t, s1, s2, o1, o2);
-                if (!isnan(o1)) C.g_v1 = o1;
-                if (!isnan(o2)) C.g_v2 = o2;
-            }
-            __syncthreads();
-            v1 = C.g_v1;
-            v2 = C.g_v2;
-            __syncthreads();
+            q.sync();
+            gpick(q, buf, cnt, q1 - below - c1, q2 - below - c1, C, v1, v2);
             return;
         }
         float nlo = FLT_MAX, nhi = -FLT_MAX;
-        for (int i = tid; i < L; i += NT) {
+        for (int i = q.t; i < L; i += GS) {
             const float a = f(i);
             if (a >= lo && a <= hi) {
                 const int b = bucket(a, lo, scale);
@@ -203,23 +246,10 @@ __device__ void select_generic(F f, int L, int q1, int q2, float lo, float hi, u
                 }
             }
         }
-        nlo = warp_min(nlo);
-        nhi = warp_max(nhi);
-        if ((tid & 31) == 0) {
-            C.fred[tid >> 5] = nlo;
-            C.fred[NWARP + (tid >> 5)] = nhi;
-        }
-        __syncthreads();
-        lo = C.fred[0];
-        hi = C.fred[NWARP];
-        for (int i = 1; i < NWARP; ++i) {
-            lo = fminf(lo, C.fred[i]);
-            hi = fmaxf(hi, C.fred[NWARP + i]);
-        }
+        gminmax(q, nlo, nhi, C, lo, hi);
         below += c1;
-        __syncthreads();
     }
-    if (tid == 0) atomicOr(err, ERR_SELECT_ITER);
+    if (q.t == 0) atomicOr(err, ERR_SELECT_ITER);
     v1 = v2 = __int_as_float(0x7FC00000);
 }
 
@@ -236,6 +266,7 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
                                                  const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
 {
+    constexpr int GS = NT / G;   // threads per direction group
     extern __shared__ __align__(16) float sm[];
     __shared__ Ctl C;
     const TaskDev T = tasks[blockIdx.x];
@@ -250,52 +281,55 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
     unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
     float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
 
-    const int GA = T.nj;   // live directions; slots GA..G-1 are inert
+    const int GA = T.nj;   // live directions; groups GA..G-1 are inert
     for (int e = tid; e < G * ldx; e += NT) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
     for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
-    if (tid < MAXG * 2) {
-        const float qnan = __int_as_float(0x7FC00000);
-        C.v1[tid >> 1][tid & 1] = qnan;
-        C.v2[tid >> 1][tid & 1] = qnan;
-    }
-    if (tid < MAXG) {
-        C.npos[tid] = 0;
-        C.fb[tid] = tid < GA ? 0 : 3;
-    }
     __syncthreads();
     // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
     // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
-    // to the edge buckets, which keeps the bucket map monotone.
-    if (tid < G) {
-        const int g = tid;
+    // to the edge buckets, which keeps the bucket map monotone.  One warp per direction: lanes
+    // take rows of Cov (the range is a heuristic, so its summation order is free); y_z keeps the
+    // keys' own arithmetic (one lane, sequential FMAs).
+    if ((tid >> 5) < G) {
+        const int g = tid >> 5, lane = tid & 31;
         const float* u = uS + g * ldx;
-        float a = 0.0f, yc = 0.0f;
-        const float* zr = z32 + S.zoff32;
-        for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);   // y_z: same arithmetic as the keys
-        for (int l = 0; l < d; ++l) yc = fmaf(u[l], D.center[l], yc);
-        float half = D.rc * 1.0001f;
-        if (D.cov) {
-            float q = 0.0f;
-            for (int r = 0; r < d; ++r) {
+        float yc = 0.0f, qf = 0.0f;
+        for (int r = lane; r < d; r += 32) {
+            yc = fmaf(u[r], D.center[r], yc);
+            if (D.cov) {
+                const float* row = D.cov + (size_t)r * d;
                 float t = 0.0f;
-                for (int c2 = 0; c2 < d; ++c2) t = fmaf(D.cov[r * d + c2], u[c2], t);
-                q = fmaf(u[r], t, q);
+                for (int c2 = 0; c2 < d; ++c2) t = fmaf(row[c2], u[c2], t);
+                qf = fmaf(u[r], t, qf);
             }
-            const float sg = sqrtf(fmaxf(q, 0.0f));
-            if (sg > 0.0f && 5.0f * sg < half) half = 5.0f * sg;
-            C.scale[g] = sg;   // kept for the deviation range
-        } else {
-            C.scale[g] = half;
         }
-        if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
-        C.yz[g] = a;
-        C.lo_b[g] = yc - half;
-        C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
-        C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            yc += __shfl_xor_sync(0xFFFFFFFFu, yc, o);
+            qf += __shfl_xor_sync(0xFFFFFFFFu, qf, o);
+        }
+        if (lane == 0) {
+            float a = 0.0f;
+            const float* zr = z32 + S.zoff32;
+            for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);   // y_z: same arithmetic as the keys
+            float half = D.rc * 1.0001f;
+            if (D.cov) {
+                const float sg = sqrtf(fmaxf(qf, 0.0f));
+                if (sg > 0.0f && 5.0f * sg < half) half = 5.0f * sg;
+                C.scale[g] = sg;   // kept for the deviation range
+            } else {
+                C.scale[g] = half;
+            }
+            if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
+            C.yz[g] = a;
+            C.lo_b[g] = yc - half;
+            C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
+            C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
+        }
     }
     __syncthreads();
 
-    // ---- pass A: keys + bucket counts ----------------------------------------------
+    // ---- pass A (whole CTA): keys + bucket counts ---------------------------------------
     {
         float of[G], sc[G];
 #pragma unroll
@@ -371,330 +405,175 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
     }
     __syncthreads();
 
+    // ---- from here on each group selects for its own direction --------------------------
+    const Grp<GS> q{tid / GS, tid % GS};
+    const int g = q.g;
+    if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
+    const float* y = keys + (size_t)g * npad;
+    unsigned* H = hist + g * NB;
+    float* B0 = buf + (size_t)(2 * g) * CAP;   // median run; FB_CAP = 2 * CAP for the fallback
+    float* B1 = B0 + CAP;                      // MAD_+ guess run (D_AP) or MAD run (D_P)
+    const float sc = C.sc_y[g], of = C.off_y[g];
     const int k1 = (n - 1) / 2, k2 = n / 2;
-    const int npos_guess = (n & 1) ? (n - 1) / 2 : n / 2;
-    // ---- bucket runs of the wanted ranks ----------------------------------------
-    for (int g = 0; g < GA; ++g) {
-        int ba, ca, bb, cb;
-        find_buckets(hist + g * NB, k1, k2, C, ba, ca, bb, cb);
-        if (tid == 0) {
-            C.b_lo[g][0] = ba;
-            C.b_hi[g][0] = bb;
-            C.c_lo[g][0] = ca;
-            C.cnt[g][0] = cb + (int)hist[g * NB + bb] - ca;
-            C.fill[g][0] = 0;
-            C.fb[g] = C.cnt[g][0] > CAP ? 1 : 0;
-        }
-        if (ap) {
-            const int base = n - npos_guess;
-            const int r3 = base + (npos_guess - 1) / 2, r4 = base + npos_guess / 2;
-            if (npos_guess > 0) {
-                find_buckets(hist + g * NB, r3, r4, C, ba, ca, bb, cb);
-                if (tid == 0) {
-                    C.b_lo[g][1] = ba;
-                    C.b_hi[g][1] = bb;
-                    C.c_lo[g][1] = ca;
-                    C.cnt[g][1] = cb + (int)hist[g * NB + bb] - ca;
-                    if (C.cnt[g][1] > CAP) C.fb[g] = 1;
-                }
-            } else if (tid == 0) {
-                C.b_lo[g][1] = 1;
-                C.b_hi[g][1] = 0;   // empty run
-                C.c_lo[g][1] = 0;
-                C.cnt[g][1] = 0;
-            }
-            if (tid == 0) C.fill[g][1] = 0;
-        }
-        __syncthreads();
-    }
+    const int n4 = n & ~3;
+    const float qnan = __int_as_float(0x7FC00000);
 
-    // ---- pass C: gather the runs ------------------------------------------------
-    {
-        int bl0[G], bw0[G], bl1[G], bw1[G];
-        float of[G], sc[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            // a run that is off gets a start no bucket index can reach: (b - start) is then
-            // never <= 0 as an unsigned number
-            const bool on = !C.fb[g];
-            of[g] = C.off_y[g];
-            sc[g] = C.sc_y[g];
-            bl0[g] = on ? C.b_lo[g][0] : (1 << 30);
-            bw0[g] = on ? C.b_hi[g][0] - C.b_lo[g][0] : 0;
-            bl1[g] = (ap && on) ? C.b_lo[g][1] : (1 << 30);
-            bw1[g] = (ap && on) ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
-        }
-        auto gather = [&](int g, float y) {
-            const int b = bucket_fma(y, sc[g], of[g]);
-            if ((unsigned)(b - bl0[g]) <= (unsigned)bw0[g]) {
+    // bucket runs of the median ranks and (D_AP) of the MAD_+ ranks under the guess that no
+    // key ties the median
+    int ba, ca, bb, cb;
+    gfind(q, H, k1, k2, C, ba, ca, bb, cb);
+    const int c_lo0 = ca, cnt0 = cb + (int)H[bb] - ca;
+    int fb = cnt0 > CAP ? 1 : 0;   // 1: fall back for every statistic, 2: only for the spread
+    const int npos_guess = (n & 1) ? (n - 1) / 2 : n / 2;
+    int c_lo1 = 0, cnt1 = 0, bl1 = 1 << 30, bw1 = 0;
+    if (ap && npos_guess > 0) {
+        const int base = n - npos_guess;
+        int b3, c3, b4, c4;
+        gfind(q, H, base + (npos_guess - 1) / 2, base + npos_guess / 2, C, b3, c3, b4, c4);
+        c_lo1 = c3;
+        cnt1 = c4 + (int)H[b4] - c3;
+        if (cnt1 > CAP) fb = 1;
+        bl1 = b3;
+        bw1 = b4 - b3;
+    }
+    float m1 = qnan, m2 = qnan, p1 = 0.f, p2 = 0.f;
+    int npos = 0;
+    if (!fb) {
+        if (q.t < 2) C.fill[g][q.t] = 0;
+        if (q.t == 0) C.pv1[g] = C.pv2[g] = qnan;
+        q.sync();
+        // a run that is off gets a start no bucket index can reach
+        const int bl0 = ba, bw0 = bb - ba;
+        if (!ap) bl1 = 1 << 30;
+        auto gather = [&](float v) {
+            const int b = bucket_fma(v, sc, of);
+            if ((unsigned)(b - bl0) <= (unsigned)bw0) {
                 const int pos = atomicAdd(&C.fill[g][0], 1);
-                if (pos < CAP) buf[(g * 2 + 0) * CAP + pos] = y;
+                if (pos < CAP) B0[pos] = v;
             }
-            if (ap && (unsigned)(b - bl1[g]) <= (unsigned)bw1[g]) {
+            if ((unsigned)(b - bl1) <= (unsigned)bw1) {
                 const int pos = atomicAdd(&C.fill[g][1], 1);
-                if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = y;
+                if (pos < CAP) B1[pos] = v;
             }
         };
-        const int n4 = n & ~3;
-        for (int i = 4 * tid; i < n4; i += 4 * NT) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
-                gather(g, y4.x);
-                gather(g, y4.y);
-                gather(g, y4.z);
-                gather(g, y4.w);
-            }
+        for (int i = 4 * q.t; i < n4; i += 4 * GS) {
+            const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+            gather(y4.x);
+            gather(y4.y);
+            gather(y4.z);
+            gather(y4.w);
         }
-        for (int i = n4 + tid; i < n; i += NT) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) gather(g, keys[(size_t)g * npad + i]);
-        }
-    }
-    __syncthreads();
-
-    // ---- exact ranks within the gathered keys -------------------------------------
-    for (int g = 0; g < G; ++g) {
-        if (C.fb[g]) continue;
-        const int cnt = C.cnt[g][0];
-        const int s1 = k1 - C.c_lo[g][0], s2 = k2 - C.c_lo[g][0];
-        for (int t = tid; t < cnt; t += NT) {
-            float o1 = __int_as_float(0x7FC00000), o2 = o1;
-            rank_pick(buf + (g * 2) * CAP, cnt, t, s1, s2, o1, o2);
-            if (!isnan(o1)) C.v1[g][0] = o1;
-            if (!isnan(o2)) C.v2[g][0] = o2;
-        }
-    }
-    if (tid < MAXG) C.nle[tid] = 0;
-    __syncthreads();
-    if (ap) {
-        // #(y <= med) = #(y <= m1): keys below the run plus gathered keys <= m1
-        for (int g = 0; g < G; ++g) {
-            if (C.fb[g]) continue;
-            const float m1 = C.v1[g][0];
+        for (int i = n4 + q.t; i < n; i += GS) gather(y[i]);
+        q.sync();
+        gpick(q, B0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2);
+        if (ap) {
+            // #(y <= med) = #(y <= m1): keys below the run plus gathered keys <= m1
             int c = 0;
-            for (int t = tid; t < C.cnt[g][0]; t += NT) c += (buf[(g * 2) * CAP + t] <= m1);
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-            if ((tid & 31) == 0 && c) atomicAdd(&C.nle[g], c);
-        }
-        __syncthreads();
-        for (int g = 0; g < G; ++g) {
-            if (C.fb[g]) continue;
-            const int nle = C.c_lo[g][0] + C.nle[g];
-            const int npos = n - nle;
-            if (tid == 0) C.npos[g] = npos;
-            if (npos == 0) continue;
-            const int base = n - npos;
-            const int r3 = base + (npos - 1) / 2, r4 = base + npos / 2;
-            const int s3 = r3 - C.c_lo[g][1], s4 = r4 - C.c_lo[g][1];
-            const int cnt = C.cnt[g][1];
-            if (s3 < 0 || s4 >= cnt) {
-                if (tid == 0) C.fb[g] = 2;   // the positive count differed from the guess
-                continue;
+            for (int t = q.t; t < cnt0; t += GS) c += (B0[t] <= m1);
+            const int nle = c_lo0 + gsum(q, c, C);
+            npos = n - nle;
+            if (npos > 0) {
+                const int s3 = nle + (npos - 1) / 2 - c_lo1, s4 = nle + npos / 2 - c_lo1;
+                if (s3 < 0 || s4 >= cnt1) {
+                    fb = 2;   // the positive count differed from the guess
+                } else {
+                    if (q.t == 0) C.pv1[g] = C.pv2[g] = qnan;
+                    q.sync();
+                    gpick(q, B1, cnt1, s3, s4, C, p1, p2);
+                }
             }
-            for (int t = tid; t < cnt; t += NT) {
-                float o1 = __int_as_float(0x7FC00000), o2 = o1;
-                rank_pick(buf + (g * 2 + 1) * CAP, cnt, t, s3, s4, o1, o2);
-                if (!isnan(o1)) C.v1[g][1] = o1;
-                if (!isnan(o2)) C.v2[g][1] = o2;
-            }
-        }
-        __syncthreads();
-    } else {
-        // ---- D_P: |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
-        for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
-        if (tid < G) {
-            const float m = __fmul_rn(__fadd_rn(C.v1[tid][0], C.v2[tid][0]), 0.5f);
-            float dmax = D.cov ? 4.0f * C.scale[tid] : 0.0f;
-            const float hard = __fmul_rn(__fadd_rn(D.rc, fabsf(m - C.lo_b[tid] - 0.5f * (float)NB / C.sc_y[tid])),
-                                         1.0001f);
+        } else {
+            // D_P: |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
+            const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
+            float dmax = D.cov ? 4.0f * C.scale[g] : 0.0f;
+            const float hard =
+                __fmul_rn(__fadd_rn(D.rc, fabsf(m - C.lo_b[g] - 0.5f * (float)NB / sc)), 1.0001f);
             if (!(dmax > 0.0f) || dmax > hard) dmax = hard;
             if (!(dmax > 0.0f)) dmax = 1.0f;
-            C.cen[tid] = m;
-            C.sc_d[tid] = __fdiv_rn((float)NB, dmax);
-        }
-        __syncthreads();
-        {
-            float cen[G], scl[G];
-            bool on[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                on[g] = !C.fb[g];
-                cen[g] = C.cen[g];
-                scl[g] = C.sc_d[g];
+            const float scd = __fdiv_rn((float)NB, dmax);
+            for (int b = q.t; b < NB; b += GS) H[b] = 0u;
+            q.sync();
+            for (int i = 4 * q.t; i < n4; i += 4 * GS) {
+                const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.x, m)), scd, 0.0f)], 1u);
+                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.y, m)), scd, 0.0f)], 1u);
+                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.z, m)), scd, 0.0f)], 1u);
+                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.w, m)), scd, 0.0f)], 1u);
             }
-            auto add = [&](int g, float y) {
-                const float dv = fabsf(__fsub_rn(y, cen[g]));
-                atomicAdd(&hist[g * NB + bucket_fma(dv, scl[g], 0.0f)], 1u);
-            };
-            const int n4 = n & ~3;
-            for (int i = 4 * tid; i < n4; i += 4 * NT) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    if (on[g]) {
-                        const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
-                        add(g, y4.x);
-                        add(g, y4.y);
-                        add(g, y4.z);
-                        add(g, y4.w);
+            for (int i = n4 + q.t; i < n; i += GS) atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y[i], m)), scd, 0.0f)], 1u);
+            q.sync();
+            int da, dca, db, dcb;
+            gfind(q, H, k1, k2, C, da, dca, db, dcb);
+            const int cntd = dcb + (int)H[db] - dca;
+            if (cntd > CAP) {
+                fb = 2;
+            } else {
+                if (q.t == 0) {
+                    C.fill[g][1] = 0;
+                    C.pv1[g] = C.pv2[g] = qnan;
+                }
+                q.sync();
+                const int bwd = db - da;
+                auto gd = [&](float v) {
+                    const float dv = fabsf(__fsub_rn(v, m));
+                    const int b = bucket_fma(dv, scd, 0.0f);
+                    if ((unsigned)(b - da) <= (unsigned)bwd) {
+                        const int pos = atomicAdd(&C.fill[g][1], 1);
+                        if (pos < CAP) B1[pos] = dv;
                     }
+                };
+                for (int i = 4 * q.t; i < n4; i += 4 * GS) {
+                    const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+                    gd(y4.x);
+                    gd(y4.y);
+                    gd(y4.z);
+                    gd(y4.w);
                 }
-            }
-            for (int i = n4 + tid; i < n; i += NT) {
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                    if (on[g]) add(g, keys[(size_t)g * npad + i]);
+                for (int i = n4 + q.t; i < n; i += GS) gd(y[i]);
+                q.sync();
+                gpick(q, B1, cntd, k1 - dca, k2 - dca, C, p1, p2);
             }
         }
-        __syncthreads();
-        for (int g = 0; g < G; ++g) {
-            if (C.fb[g]) continue;
-            int ba, ca, bb, cb;
-            find_buckets(hist + g * NB, k1, k2, C, ba, ca, bb, cb);
-            if (tid == 0) {
-                C.b_lo[g][1] = ba;
-                C.b_hi[g][1] = bb;
-                C.c_lo[g][1] = ca;
-                C.cnt[g][1] = cb + (int)hist[g * NB + bb] - ca;
-                C.fill[g][1] = 0;
-                if (C.cnt[g][1] > CAP) C.fb[g] = 2;
-            }
-            __syncthreads();
-        }
-        {
-            float cen[G], scl[G];
-            int bl[G], bw[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                cen[g] = C.cen[g];
-                scl[g] = C.sc_d[g];
-                bl[g] = !C.fb[g] ? C.b_lo[g][1] : (1 << 30);
-                bw[g] = !C.fb[g] ? C.b_hi[g][1] - C.b_lo[g][1] : 0;
-            }
-            auto gather = [&](int g, float y) {
-                const float dv = fabsf(__fsub_rn(y, cen[g]));
-                const int b = bucket_fma(dv, scl[g], 0.0f);
-                if ((unsigned)(b - bl[g]) <= (unsigned)bw[g]) {
-                    const int pos = atomicAdd(&C.fill[g][1], 1);
-                    if (pos < CAP) buf[(g * 2 + 1) * CAP + pos] = dv;
-                }
-            };
-            const int n4 = n & ~3;
-            for (int i = 4 * tid; i < n4; i += 4 * NT) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const float4 y4 = *reinterpret_cast<const float4*>(keys + (size_t)g * npad + i);
-                    gather(g, y4.x);
-                    gather(g, y4.y);
-                    gather(g, y4.z);
-                    gather(g, y4.w);
-                }
-            }
-            for (int i = n4 + tid; i < n; i += NT) {
-#pragma unroll
-                for (int g = 0; g < G; ++g) gather(g, keys[(size_t)g * npad + i]);
-            }
-        }
-        __syncthreads();
-        for (int g = 0; g < G; ++g) {
-            if (C.fb[g]) continue;
-            const int cnt = C.cnt[g][1];
-            const int s1 = k1 - C.c_lo[g][1], s2 = k2 - C.c_lo[g][1];
-            for (int t = tid; t < cnt; t += NT) {
-                float o1 = __int_as_float(0x7FC00000), o2 = o1;
-                rank_pick(buf + (g * 2 + 1) * CAP, cnt, t, s1, s2, o1, o2);
-                if (!isnan(o1)) C.v1[g][1] = o1;
-                if (!isnan(o2)) C.v2[g][1] = o2;
-            }
-        }
-        __syncthreads();
     }
 
-    // ---- fallback directions: iterated bucket selection over their keys ---------
-    for (int g = 0; g < G; ++g) {
-        const int fb = C.fb[g];
-        if (fb == 0 || fb == 3) continue;
-        const float* y = keys + (size_t)g * npad;
-        // exact range of this direction's keys
+    // ---- fallback: iterated bucket selection over this direction's keys ----------------
+    if (fb) {
         float kl = FLT_MAX, kh = -FLT_MAX;
-        for (int i = tid; i < n; i += NT) {
+        for (int i = q.t; i < n; i += GS) {
             kl = fminf(kl, y[i]);
             kh = fmaxf(kh, y[i]);
         }
-        kl = warp_min(kl);
-        kh = warp_max(kh);
-        __syncthreads();
-        if ((tid & 31) == 0) {
-            C.fred[tid >> 5] = kl;
-            C.fred[NWARP + (tid >> 5)] = kh;
-        }
-        __syncthreads();
-        kl = C.fred[0];
-        kh = C.fred[NWARP];
-        for (int i = 1; i < NWARP; ++i) {
-            kl = fminf(kl, C.fred[i]);
-            kh = fmaxf(kh, C.fred[NWARP + i]);
-        }
-        __syncthreads();
-        float m1, m2;
-        if (fb == 1) {
-            select_generic([&](int i) { return y[i]; }, n, k1, k2, kl, kh, hist, buf, C, m1, m2, err);
-            if (tid == 0) {
-                C.v1[g][0] = m1;
-                C.v2[g][0] = m2;
-            }
-            __syncthreads();
-        } else {
-            m1 = C.v1[g][0];
-            m2 = C.v2[g][0];
-        }
+        gminmax(q, kl, kh, C, kl, kh);
+        unsigned* HF = H;
+        float* BF = B0;   // FB_CAP floats: B0 and B1
+        if (fb == 1) gselect(q, [&](int i) { return y[i]; }, n, k1, k2, kl, kh, HF, BF, C, m1, m2, err);
         if (ap) {
             int c = 0;
-            for (int i = tid; i < n; i += NT) c += (y[i] <= m1);
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-            __syncthreads();
-            if ((tid & 31) == 0) C.red[tid >> 5] = c;
-            __syncthreads();
-            int nle = 0;
-            for (int i = 0; i < NWARP; ++i) nle += C.red[i];
-            const int npos = n - nle;
-            if (tid == 0) C.npos[g] = npos;
-            float p1 = m1, p2 = m1;
+            for (int i = q.t; i < n; i += GS) c += (y[i] <= m1);
+            const int nle = gsum(q, c, C);
+            npos = n - nle;
+            p1 = p2 = m1;
             if (npos > 0)
-                select_generic([&](int i) { return y[i]; }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, hist,
-                               buf, C, p1, p2, err);
-            if (tid == 0) {
-                C.v1[g][1] = p1;
-                C.v2[g][1] = p2;
-            }
+                gselect(q, [&](int i) { return y[i]; }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, HF, BF, C,
+                        p1, p2, err);
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
             const float dmax = fmaxf(fabsf(__fsub_rn(kl, m)), fabsf(__fsub_rn(kh, m)));
-            float a1, a2;
-            select_generic([&](int i) { return fabsf(__fsub_rn(y[i], m)); }, n, k1, k2, 0.0f, dmax, hist, buf, C, a1,
-                           a2, err);
-            if (tid == 0) {
-                C.v1[g][1] = a1;
-                C.v2[g][1] = a2;
-            }
+            gselect(q, [&](int i) { return fabsf(__fsub_rn(y[i], m)); }, n, k1, k2, 0.0f, dmax, HF, BF, C, p1, p2,
+                    err);
         }
-        __syncthreads();
     }
 
-    // ---- depths (FP64 on a handful of values) --------------------------------------
-    if (tid < GA) {
-        const int g = tid;
-        const double med = ((double)C.v1[g][0] + (double)C.v2[g][0]) * 0.5;
+    // ---- depth (FP64 on a handful of values) ----------------------------------------------
+    if (q.t == 0) {
+        const double med = ((double)m1 + (double)m2) * 0.5;
         const double yzv = (double)C.yz[g];
         double depth;
         if (ap) {
-            const double madp =
-                C.npos[g] > 0 ? (((double)C.v1[g][1] - med) + ((double)C.v2[g][1] - med)) * 0.5 : 0.0;
+            const double madp = npos > 0 ? (((double)p1 - med) + ((double)p2 - med)) * 0.5 : 0.0;
             depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
         } else {
-            const double mad = ((double)C.v1[g][1] + (double)C.v2[g][1]) * 0.5;
+            const double mad = ((double)p1 + (double)p2) * 0.5;
             depth = depth_from(fabs(yzv - med), mad);
         }
         res[S.roff + T.j0 + g] = ResDev{depth, -1};
