@@ -129,15 +129,21 @@ __device__ void gminmax(const Grp<GS>& q, float lo, float hi, Ctl& C, float& olo
 template <int GS>
 __device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, Ctl& C, int& ba, int& ca, int& bb, int& cb)
 {
-    constexpr int PER = NB / GS;
+    constexpr int PER = NB / GS;   // 4, 8 or 16 consecutive buckets per thread, read as uint4
     const int lane = q.t & 31, w = q.t >> 5;
     int own = 0;
     unsigned v[PER];
+    const uint4* h4 = reinterpret_cast<const uint4*>(h + q.t * PER);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        v[k] = h[q.t * PER + k];
-        own += (int)v[k];
+    for (int k = 0; k < PER / 4; ++k) {
+        const uint4 a = h4[k];
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
     }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) own += (int)v[k];
     int incl = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -208,7 +214,7 @@ __device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, 
         }
         float scale = __fdiv_rn((float)FB_NB, __fsub_rn(hi, lo));
         if (!(scale <= FLT_MAX)) scale = FLT_MAX;
-        for (int b = q.t; b < FB_NB; b += GS) hist[b] = 0u;
+        for (int b = q.t; b < FB_NB / 4; b += GS) reinterpret_cast<uint4*>(hist)[b] = make_uint4(0u, 0u, 0u, 0u);
         q.sync();
         for (int i = q.t; i < L; i += GS) {
             const float a = f(i);
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
 
     const int GA = T.nj;   // live directions; groups GA..G-1 are inert
     for (int e = tid; e < G * ldx; e += NT) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
-    for (int e = tid; e < G * NB; e += NT) hist[e] = 0u;
+    for (int e = tid; e < G * NB / 4; e += NT) reinterpret_cast<uint4*>(hist)[e] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
     // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
             if (!(dmax > 0.0f) || dmax > hard) dmax = hard;
             if (!(dmax > 0.0f)) dmax = 1.0f;
             const float scd = __fdiv_rn((float)NB, dmax);
-            for (int b = q.t; b < NB; b += GS) H[b] = 0u;
+            for (int b = q.t; b < NB / 4; b += GS) reinterpret_cast<uint4*>(H)[b] = make_uint4(0u, 0u, 0u, 0u);
             q.sync();
             for (int i = 4 * q.t; i < n4; i += 4 * GS) {
                 const float4 y4 = *reinterpret_cast<const float4*>(y + i);
