@@ -6,7 +6,7 @@
 // shared memory.  The whole CTA projects (pass A: every point on the G
 // directions, keys stored, each added to a 2048-bucket histogram over
 // u'c +- 5 sigma_u, bucket = monotone FP32 map of the key).  Then the CTA
-// splits into G groups of NT/G threads, one per direction, each synchronising
+// splits into G groups of (CTA threads)/G, one per direction, each synchronising
 // on its own named barrier, so the directions never wait for one another:
 //   median  find the buckets of the median ranks, gather their keys (and, for
 //           D_AP, the keys of the buckets expected to hold the MAD_+ ranks),
@@ -27,8 +27,14 @@
 namespace rrs {
 namespace {
 
-constexpr int NT = 512;
-constexpr int NWARP = NT / 32;
+constexpr int NT = 512;              // threads per CTA for G = 1, 2 (two CTAs per SM)
+constexpr int NT4 = 1024;            // threads per CTA for G = 4 (one CTA per SM)
+constexpr int NWARP = NT4 / 32;      // largest warp count of a CTA
+template <int G>
+__host__ __device__ constexpr int cta_threads()
+{
+    return G == 4 ? NT4 : NT;
+}
 constexpr int NB = 2048;     // buckets per direction
 constexpr int CAP = 256;     // gathered keys per direction and target
 constexpr int MAXG = 4;
@@ -36,7 +42,7 @@ constexpr int FB_NB = NB;    // fallback histogram (reuses the bucket area)
 constexpr int FB_CAP = 2 * CAP;  // fallback gather buffer: a direction's two gather areas
 
 // Per-direction constants and per-group scratch: after the projection pass,
-// group g (NT / G threads) works on direction g alone and synchronises with
+// group g (CTA threads / G) works on direction g alone and synchronises with
 // the named barrier 1 + g, so the directions of a CTA never wait for each other.
 struct Ctl {
     float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: about (y - lo_b) * sc_y
@@ -265,153 +271,29 @@ __device__ __forceinline__ double depth_from(double num, double spread)
     return 1.0 / (1.0 + num / spread);
 }
 
-// G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
-// directions are then held in registers), 0 for any d.
-template <int G, int DP4>
-__global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
-                                                 const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
+// Key u'x for d <= 16 (DP4 = d rounded up to 4): two sequential FMA chains over the two
+// halves of the DP4 dims, added (two independent chains per key).  Keys and y_z are formed
+// the same way whatever the group size, so results never depend on it.
+template <int DP4>
+__device__ __forceinline__ float key_halves(const float* u, const float* x)
 {
-    constexpr int GS = NT / G;   // threads per direction group
-    extern __shared__ __align__(16) float sm[];
-    __shared__ Ctl C;
-    const TaskDev T = tasks[blockIdx.x];
-    const SlotDev& S = slots[T.slot];
-    const DsDev D = dsets[S.ds];
-    const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = DP4 ? DP4 : ((d + 3) & ~3);
-    const bool ap = (S.kind == 2);
+    float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+    for (int l = 0; l < DP4 / 2; ++l) p0 = fmaf(u[l], x[l], p0);
+#pragma unroll
+    for (int l = DP4 / 2; l < DP4; ++l) p1 = fmaf(u[l], x[l], p1);
+    return __fadd_rn(p0, p1);
+}
+
+// Exact median / MAD / MAD_+ of each live direction's keys (after the projection
+// pass) and the depth: group g of cta_threads<G>() / G threads handles direction g alone.
+template <int G>
+__device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned* hist, float* buf, int n, int npad,
+                                            bool ap, const DsDev& D, int GA, int64_t roff, ResDev* __restrict__ res,
+                                            int* err)
+{
+    constexpr int GS = cta_threads<G>() / G;   // threads per direction group
     const int tid = threadIdx.x;
-    const int npad = (n + 3) & ~3;
-    float* keys = sm;                                          // G x npad
-    float* uS = keys + (size_t)G * npad;                       // G x ldx
-    unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
-    float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
-
-    const int GA = T.nj;   // live directions; groups GA..G-1 are inert
-    for (int e = tid; e < G * ldx; e += NT) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
-    for (int e = tid; e < G * NB / 4; e += NT) reinterpret_cast<uint4*>(hist)[e] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
-    // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
-    // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
-    // to the edge buckets, which keeps the bucket map monotone.  One warp per direction: lanes
-    // take rows of Cov (the range is a heuristic, so its summation order is free); y_z keeps the
-    // keys' own arithmetic (one lane, sequential FMAs).
-    if ((tid >> 5) < G) {
-        const int g = tid >> 5, lane = tid & 31;
-        const float* u = uS + g * ldx;
-        float yc = 0.0f, qf = 0.0f;
-        for (int r = lane; r < d; r += 32) {
-            yc = fmaf(u[r], D.center[r], yc);
-            if (D.cov) {
-                const float* row = D.cov + (size_t)r * d;
-                float t = 0.0f;
-                for (int c2 = 0; c2 < d; ++c2) t = fmaf(row[c2], u[c2], t);
-                qf = fmaf(u[r], t, qf);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            yc += __shfl_xor_sync(0xFFFFFFFFu, yc, o);
-            qf += __shfl_xor_sync(0xFFFFFFFFu, qf, o);
-        }
-        if (lane == 0) {
-            float a = 0.0f;
-            const float* zr = z32 + S.zoff32;
-            for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);   // y_z: same arithmetic as the keys
-            float half = D.rc * 1.0001f;
-            if (D.cov) {
-                const float sg = sqrtf(fmaxf(qf, 0.0f));
-                if (sg > 0.0f && 5.0f * sg < half) half = 5.0f * sg;
-                C.scale[g] = sg;   // kept for the deviation range
-            } else {
-                C.scale[g] = half;
-            }
-            if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
-            C.yz[g] = a;
-            C.lo_b[g] = yc - half;
-            C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
-            C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
-        }
-    }
-    __syncthreads();
-
-    // ---- pass A (whole CTA): keys + bucket counts ---------------------------------------
-    {
-        float of[G], sc[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            of[g] = C.off_y[g];
-            sc[g] = C.sc_y[g];
-        }
-        auto emit = [&](int i, const float (&acc)[G]) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                keys[(size_t)g * npad + i] = acc[g];
-                atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
-            }
-        };
-        if (DP4 > 0) {
-            float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
-            // two points per iteration: both rows' loads are in flight together
-            for (int i = tid; i < n; i += 2 * NT) {
-                const int i2 = i + NT;
-                const bool two = i2 < n;
-                const float4* xa = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-                const float4* xb = reinterpret_cast<const float4*>(D.X32 + (int64_t)(two ? i2 : i) * ldx);
-                float4 va[DP4 > 0 ? DP4 / 4 : 1], vb[DP4 > 0 ? DP4 / 4 : 1];
-#pragma unroll
-                for (int c = 0; c < DP4 / 4; ++c) {
-                    va[c] = xa[c];
-                    vb[c] = xb[c];
-                }
-                float acc[G], acc2[G];
-#pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = acc2[g] = 0.f;
-#pragma unroll
-                for (int c = 0; c < DP4 / 4; ++c) {
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        acc[g] = fmaf(ur[g][c].x, va[c].x, acc[g]);
-                        acc[g] = fmaf(ur[g][c].y, va[c].y, acc[g]);
-                        acc[g] = fmaf(ur[g][c].z, va[c].z, acc[g]);
-                        acc[g] = fmaf(ur[g][c].w, va[c].w, acc[g]);
-                        acc2[g] = fmaf(ur[g][c].x, vb[c].x, acc2[g]);
-                        acc2[g] = fmaf(ur[g][c].y, vb[c].y, acc2[g]);
-                        acc2[g] = fmaf(ur[g][c].z, vb[c].z, acc2[g]);
-                        acc2[g] = fmaf(ur[g][c].w, vb[c].w, acc2[g]);
-                    }
-                }
-                emit(i, acc);
-                if (two) emit(i2, acc2);
-            }
-        } else {
-            for (int i = tid; i < n; i += NT) {
-                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-                float acc[G];
-#pragma unroll
-                for (int g = 0; g < G; ++g) acc[g] = 0.f;
-                for (int l = 0; l < dp4; l += 4) {
-                    const float4 x = xr[l >> 2];
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const float4 u = *reinterpret_cast<const float4*>(uS + g * ldx + l);
-                        acc[g] = fmaf(u.x, x.x, acc[g]);
-                        acc[g] = fmaf(u.y, x.y, acc[g]);
-                        acc[g] = fmaf(u.z, x.z, acc[g]);
-                        acc[g] = fmaf(u.w, x.w, acc[g]);
-                    }
-                }
-                emit(i, acc);
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---- from here on each group selects for its own direction --------------------------
     const Grp<GS> q{tid / GS, tid % GS};
     const int g = q.g;
     if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
@@ -582,8 +464,196 @@ __global__ void __launch_bounds__(NT, (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* _
             const double mad = ((double)p1 + (double)p2) * 0.5;
             depth = depth_from(fabs(yzv - med), mad);
         }
-        res[S.roff + T.j0 + g] = ResDev{depth, -1};
+        res[roff + g] = ResDev{depth, -1};
     }
+}
+
+// G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
+// directions are then held in registers), 0 for any d.
+template <int G, int DP4>
+__global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
+                                                 const DsDev* __restrict__ dsets, const float* __restrict__ U,
+                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ Ctl C;
+    const TaskDev T = tasks[blockIdx.x];
+    const SlotDev& S = slots[T.slot];
+    const DsDev D = dsets[S.ds];
+    const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = DP4 ? DP4 : ((d + 3) & ~3);
+    const bool ap = (S.kind == 2);
+    const int tid = threadIdx.x;
+    const int npad = (n + 3) & ~3;
+    float* keys = sm;                                          // G x npad
+    float* uS = keys + (size_t)G * npad;                       // G x ldx
+    unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
+    float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
+
+    const int GA = T.nj;   // live directions; groups GA..G-1 are inert
+    constexpr int NTK = cta_threads<G>();
+    for (int e = tid; e < G * ldx; e += NTK) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
+    for (int e = tid; e < G * NB / 4; e += NTK) reinterpret_cast<uint4*>(hist)[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
+    // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
+    // to the edge buckets, which keeps the bucket map monotone.  One warp per direction: lanes
+    // take rows of Cov (the range is a heuristic, so its summation order is free); y_z keeps the
+    // keys' own arithmetic (one lane, sequential FMAs).
+    if ((tid >> 5) < G) {
+        const int g = tid >> 5, lane = tid & 31;
+        const float* u = uS + g * ldx;
+        float yc = 0.0f, qf = 0.0f;
+        for (int r = lane; r < d; r += 32) {
+            yc = fmaf(u[r], D.center[r], yc);
+            if (D.cov) {
+                const float* row = D.cov + (size_t)r * d;
+                float t = 0.0f;
+                for (int c2 = 0; c2 < d; ++c2) t = fmaf(row[c2], u[c2], t);
+                qf = fmaf(u[r], t, qf);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            yc += __shfl_xor_sync(0xFFFFFFFFu, yc, o);
+            qf += __shfl_xor_sync(0xFFFFFFFFu, qf, o);
+        }
+        if (lane == 0) {
+            float a = 0.0f;
+            const float* zr = z32 + S.zoff32;
+            if (DP4 > 0) {
+                a = key_halves<(DP4 > 0 ? DP4 : 4)>(u, zr);   // y_z: same arithmetic as the keys
+            } else {
+                for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);
+            }
+            float half = D.rc * 1.0001f;
+            if (D.cov) {
+                const float sg = sqrtf(fmaxf(qf, 0.0f));
+                if (sg > 0.0f && 5.0f * sg < half) half = 5.0f * sg;
+                C.scale[g] = sg;   // kept for the deviation range
+            } else {
+                C.scale[g] = half;
+            }
+            if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
+            C.yz[g] = a;
+            C.lo_b[g] = yc - half;
+            C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
+            C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
+        }
+    }
+    __syncthreads();
+
+    // ---- pass A (whole CTA): keys + bucket counts ---------------------------------------
+    {
+        float of[G], sc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            of[g] = C.off_y[g];
+            sc[g] = C.sc_y[g];
+        }
+        auto emit = [&](int i, const float (&acc)[G]) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                keys[(size_t)g * npad + i] = acc[g];
+                atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
+            }
+        };
+        if (G == 4 && DP4 > 0) {
+            // two adjacent lanes per point, each forming the keys of two directions: the row load is
+            // coalesced within the warp and each lane holds only two direction vectors
+            constexpr int D4 = DP4 > 0 ? DP4 : 4;
+            const int pair = tid & 1;
+            float ua[D4], ub[D4];
+#pragma unroll
+            for (int l = 0; l < D4; ++l) {
+                ua[l] = uS[(2 * pair) * ldx + l];
+                ub[l] = uS[(2 * pair + 1) * ldx + l];
+            }
+            const float sca = sc[2 * pair], ofa = of[2 * pair], scb = sc[2 * pair + 1], ofb = of[2 * pair + 1];
+            for (int i = tid >> 1; i < n; i += NTK / 2) {
+                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                float xv[D4];
+#pragma unroll
+                for (int c = 0; c < D4 / 4; ++c) {
+                    const float4 t4 = xr[c];
+                    xv[4 * c] = t4.x;
+                    xv[4 * c + 1] = t4.y;
+                    xv[4 * c + 2] = t4.z;
+                    xv[4 * c + 3] = t4.w;
+                }
+                const float ka = key_halves<D4>(ua, xv), kb = key_halves<D4>(ub, xv);
+                keys[(size_t)(2 * pair) * npad + i] = ka;
+                atomicAdd(&hist[(2 * pair) * NB + bucket_fma(ka, sca, ofa)], 1u);
+                keys[(size_t)(2 * pair + 1) * npad + i] = kb;
+                atomicAdd(&hist[(2 * pair + 1) * NB + bucket_fma(kb, scb, ofb)], 1u);
+            }
+        } else if (DP4 > 0) {
+            float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
+            // two points per iteration: both rows' loads are in flight together
+            for (int i = tid; i < n; i += 2 * NTK) {
+                const int i2 = i + NTK;
+                const bool two = i2 < n;
+                const float4* xa = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                const float4* xb = reinterpret_cast<const float4*>(D.X32 + (int64_t)(two ? i2 : i) * ldx);
+                float4 va[DP4 > 0 ? DP4 / 4 : 1], vb[DP4 > 0 ? DP4 / 4 : 1];
+#pragma unroll
+                for (int c = 0; c < DP4 / 4; ++c) {
+                    va[c] = xa[c];
+                    vb[c] = xb[c];
+                }
+                float acc[G], acc2[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    // key_halves on the register copies (one row's dims as plain floats)
+                    float uu[DP4 > 0 ? DP4 : 4], xa_[DP4 > 0 ? DP4 : 4], xb_[DP4 > 0 ? DP4 : 4];
+#pragma unroll
+                    for (int c = 0; c < DP4 / 4; ++c) {
+                        uu[4 * c] = ur[g][c].x;
+                        uu[4 * c + 1] = ur[g][c].y;
+                        uu[4 * c + 2] = ur[g][c].z;
+                        uu[4 * c + 3] = ur[g][c].w;
+                        xa_[4 * c] = va[c].x;
+                        xa_[4 * c + 1] = va[c].y;
+                        xa_[4 * c + 2] = va[c].z;
+                        xa_[4 * c + 3] = va[c].w;
+                        xb_[4 * c] = vb[c].x;
+                        xb_[4 * c + 1] = vb[c].y;
+                        xb_[4 * c + 2] = vb[c].z;
+                        xb_[4 * c + 3] = vb[c].w;
+                    }
+                    acc[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xa_);
+                    acc2[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xb_);
+                }
+                emit(i, acc);
+                if (two) emit(i2, acc2);
+            }
+        } else {
+            for (int i = tid; i < n; i += NTK) {
+                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+                float acc[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = 0.f;
+                for (int l = 0; l < dp4; l += 4) {
+                    const float4 x = xr[l >> 2];
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const float4 u = *reinterpret_cast<const float4*>(uS + g * ldx + l);
+                        acc[g] = fmaf(u.x, x.x, acc[g]);
+                        acc[g] = fmaf(u.y, x.y, acc[g]);
+                        acc[g] = fmaf(u.z, x.z, acc[g]);
+                        acc[g] = fmaf(u.w, x.w, acc[g]);
+                    }
+                }
+                emit(i, acc);
+            }
+        }
+    }
+    __syncthreads();
+
+    select_dirs<G>(C, keys, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err);
 }
 
 }  // namespace
@@ -597,19 +667,26 @@ size_t pdap_smem_bytes(int n, int group, int ldx)
 
 size_t pdap_smem_limit()
 {
-    // opt-in maximum per CTA (227 KB) minus the kernel's static control block
-    return 232448 - sizeof(Ctl) - 256;
+    // opt-in maximum per CTA (227 KB) minus the kernels' static blocks
+    return 232448 - sizeof(Ctl) - 64 - 256;
+}
+
+size_t pdap_two_per_sm_limit()
+{
+    // 228 KB per SM shared by two CTAs, each also holding 1 KB of reserved and ~1 KB of static memory
+    return 112 * 1024;
 }
 
 int pdap_max_group(int n, int ldx, int m)
 {
     // G in {1, 2, 4}: the largest that fits two CTAs per SM when that is at least 2, else the
     // largest that fits one CTA per SM
-    const size_t one = pdap_smem_limit(), two = 110 * 1024;
+    const size_t one = pdap_smem_limit(), two = pdap_two_per_sm_limit();
     int g_one = 0, g_two = 0;
     for (int g = 1; g <= MAXG && g <= m; g *= 2) {
-        if (pdap_smem_bytes(n, g, ldx) <= one) g_one = g;
-        if (pdap_smem_bytes(n, g, ldx) <= two) g_two = g;
+        const size_t need = pdap_smem_bytes(n, g, ldx);
+        if (need <= one) g_one = g;
+        if (need <= two) g_two = g;
     }
     if (g_two >= 2) return g_two;
     return g_one;
@@ -624,7 +701,7 @@ static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<G, DP4><<<ntasks, NT, smem, st>>>(tasks, slots, ds, U, z32, res, err);
+    k_pdap2<G, DP4><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err);
     return cudaGetLastError();
 }
 

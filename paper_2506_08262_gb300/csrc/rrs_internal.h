@@ -2,6 +2,7 @@
 // translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,6 +84,11 @@ enum : int {
 // (FP64 inputs), of y_z to FP32 and of the final difference; twice that sum for slack.
 __host__ __device__ inline float band_gamma_fp32(int d) { return (float)((double)(d + 4) * 0x1p-23); }
 float band_gamma_tc(int kp);
+// cuTensorMapEncodeTiled, looked up once through the runtime (NULL when unavailable)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn();
 float band_coef_ff(int d);   // bound coefficient of the compensated FP32 re-check (tensor-core path)
 
 // Set the text that rrs_last_error() returns on this thread (rrs_api.cu).
@@ -123,7 +129,7 @@ cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* c
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx);
 size_t pdap_smem_limit();
-int pdap_max_group(int n, int ldx, int m);
+int pdap_max_group(int n, int ldx, int m);   // largest feasible G (0 if none)
 
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
