@@ -120,7 +120,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_us
 __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 
 struct TcShared {
-    uint64_t full[STAGES], empty[STAGES], acc_full[MAXACC], acc_empty[MAXACC];
+    uint64_t full[STAGES], acc_full[MAXACC], acc_empty[MAXACC];
     uint32_t tmem_base;
     int abort;
     int mma_tiles;   // tiles whose operands the MMA issuer has consumed
@@ -275,7 +275,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
             mbar_init(&sh.full[s], 1);
-            mbar_init(&sh.empty[s], 1);
         }
         sh.mma_tiles = 0;
         for (int b = 0; b < NACC; ++b) {
@@ -302,7 +301,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int issued = 0;
             for (int t = 0; t < ntiles; ++t) {
                 const int s = t % nst;
-                if (t >= nst && !mbar_wait(&sh.empty[s], ((t / nst) - 1) & 1, err)) {
+                // stage s is free once the MMAs of tile t - nst have completed, which the accumulator's
+                // full barrier of that tile reports (one commit per tile serves both)
+                const int u = t - nst;
+                if (t >= nst && !mbar_wait(&sh.acc_full[u % NACC], (u / NACC) & 1, err)) {
                     atomicOr(err, ERR_TIMEOUT);
                     sh.abort = 1;
                     break;
@@ -354,7 +356,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                umma_commit(&sh.empty[s]);
                 umma_commit(&sh.acc_full[b]);
                 *(volatile int*)&sh.mma_tiles = t + 1;
             }
