@@ -265,10 +265,17 @@ __device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, 
     v1 = v2 = __int_as_float(0x7FC00000);
 }
 
+// 1 / (1 + num / spread) = spread / (spread + num) for num, spread >= 0 (FP64 inputs, exact differences
+// of FP32 order statistics).  GB300 issues FP64 at a fraction of the FP32 rate, so the one division is
+// done in FP32 (relative error a few 2^-24) whenever both operands and the quotient are safely normal
+// FP32 numbers, and in FP64 otherwise.
 __device__ __forceinline__ double depth_from(double num, double spread)
 {
     if (spread == 0.0) return num == 0.0 ? 1.0 : 0.0;
-    return 1.0 / (1.0 + num / spread);
+    const double den = spread + num;
+    if (spread >= 1e-30 && den <= 1e30 && spread >= 1e-20 * den)
+        return (double)__fdiv_rn((float)spread, (float)den);
+    return spread / den;
 }
 
 // Key u'x for d <= 16 (DP4 = d rounded up to 4): two sequential FMA chains over the two
