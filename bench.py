@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
-                         "c4: 256 datasets batched in one graph-captured launch sequence")
+                         "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
+                         "grid: the paper's projection-depth timing grid (its Tables 1 and 2)")
     ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
     ap.add_argument("--rate", type=float, default=2000.0, help="c5: Poisson arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=3.0, help="c5: arrival window (s)")
@@ -696,6 +697,89 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's per-point projection-depth times in seconds (RTX 4080): Table 1 (n = 10,000, r = 1) and
+# Table 2 (n = 10,000, k = 250,000), columns d = 5, 10, 25, 50, 75, 100, 125, 150.
+PAPER_GRID_D = (5, 10, 25, 50, 75, 100, 125, 150)
+PAPER_TABLE1 = {
+    1_000: (0.01,) * 8, 2_500: (0.01,) * 8, 5_000: (0.02,) * 8, 10_000: (0.03,) * 8,
+    25_000: (0.06, 0.07, 0.07, 0.07, 0.07, 0.07, 0.07, 0.08),
+    50_000: (0.13, 0.14, 0.14, 0.14, 0.14, 0.15, 0.15, 0.16),
+    100_000: (0.26, 0.28, 0.28, 0.30, 0.28, 0.28, 0.30, 0.30),
+    250_000: (2.49, 2.49, 2.52, 2.59, 2.60, 2.60, 2.64, 2.66),
+}
+PAPER_TABLE2 = {  # k = 250,000; key = refinements r
+    10: (0.62, 0.67, 0.67, 0.69, 0.69, 0.69, 0.74, 0.76),
+    25: (0.61, 0.65, 0.65, 0.68, 0.69, 0.69, 0.70, 0.71),
+    50: (0.61, 0.65, 0.65, 0.67, 0.68, 0.68, 0.70, 0.73),
+    100: (0.66, 0.67, 0.67, 0.68, 0.70, 0.69, 0.71, 0.72),
+}
+
+
+def run_grid(args):
+    """Projection depth on the paper's timing grid: n = 10,000 Gaussian points with Toeplitz covariance
+    (the paper's generator), one query point at a time (latency) and 32 points per call (time per point),
+    every k of Table 1 at r = 1 and every r of Table 2 at k = 250,000, for d = 5 ... 150."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    ctx = rrs.rrs_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    n, batch = 10_000, 32
+    rows = []
+    sampler = ClockSampler(0)
+    sampler.start()
+
+    def time_call(did, Z, nq, k, r, reps):
+        dep = torch.empty(nq, dtype=torch.float64, device=dev)
+        fn = lambda: rrs.rrs_depth(ctx, did, Z, nq, rrs.RRS_F32, True, rrs.RRS_PROJECTION, k, r, 0.9, 0,
+                                   rrs.RRS_PREC_FP32_SIMT, dep, None, None, None, True, stream)
+        fn()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return min(x.elapsed_time(y) for x, y in evs)
+
+    for di, d in enumerate(PAPER_GRID_D):
+        X, Z = workloads.toeplitz_gaussian(1000 + d, n, d, batch)
+        did = rrs.rrs_register_dataset(ctx, torch.from_numpy(X).to(dev), n, d, rrs.RRS_F32, True)
+        Zd = torch.from_numpy(Z).to(dev)
+        cells = [(k, 1, PAPER_TABLE1[k][di]) for k in sorted(PAPER_TABLE1)]
+        cells += [(250_000, r, PAPER_TABLE2[r][di]) for r in sorted(PAPER_TABLE2)]
+        for k, r, paper_s in cells:
+            reps = 2 if k >= 250_000 else (3 if k >= 100_000 else 5)
+            nb = 8 if k >= 250_000 else batch   # bounded run time: 8 points per call at k = 250,000
+            one = time_call(did, Zd, 1, k, r, reps)
+            many = time_call(did, Zd, nb, k, r, reps) / nb
+            rows.append({"d": d, "k": k, "r": r, "paper_s_per_point": paper_s, "ms_one_point": round(one, 4),
+                         "batch": nb, "ms_per_point_batched": round(many, 4),
+                         "speedup_one_point": round(paper_s * 1000 / one, 1),
+                         "speedup_batched": round(paper_s * 1000 / many, 1)})
+        rrs.rrs_free(ctx, did)
+    clocks = sampler.stop()
+    rrs.rrs_check(ctx, stream)
+    rrs.rrs_destroy(ctx)
+    sp1 = [r_["speedup_one_point"] for r_ in rows]
+    spb = [r_["speedup_batched"] for r_ in rows]
+    line = {"metric": "projection depth time per query point (paper's timing grid)", "value": None,
+            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper timing grid: D_P, n = 10,000 N(0, Toeplitz 2^-|i-j|), d in 5..150, "
+                                   "r = 1 with k = 1,000..250,000, and k = 250,000 with r = 10..100",
+                       "batch": "32 points per call (8 at k = 250,000)",
+                       "timing": "CUDA events around rrs_depth, best of 2-5 after one warm-up"},
+            "speedup_vs_paper_one_point": {"min": min(sp1), "median": float(np.median(sp1)), "max": max(sp1)},
+            "speedup_vs_paper_batched": {"min": min(spb), "median": float(np.median(spb)), "max": max(spb)},
+            "paper_hardware": "RTX 4080 laptop GPU (context only)", "rows": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -706,6 +790,8 @@ def main():
         run_c4(args)
     elif args.workload == "c5":
         run_c5(args)
+    elif args.workload == "grid":
+        run_grid(args)
     else:
         run_ours(args)
 

@@ -265,7 +265,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
                 if (it != P.tune->end()) G = it->second;
             }
             if (G && (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())) G = 0;
-            if (!G) G = pdap_max_group((int)D.n, D.ldx, m);
+            if (!G) G = pdap_max_group((int)D.n, D.ldx, m, D.d);
             if (G == 0)
                 return fail(RRS_ERR_UNSUPPORTED,
                             "projection depth needs n*4 bytes of shared memory per direction; n=%lld is too large",

@@ -129,7 +129,7 @@ cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* c
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx);
 size_t pdap_smem_limit();
-int pdap_max_group(int n, int ldx, int m);   // largest feasible G (0 if none)
+int pdap_max_group(int n, int ldx, int m, int d);   // preferred G (0 if none fits)
 
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,

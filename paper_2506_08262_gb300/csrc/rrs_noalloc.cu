@@ -197,7 +197,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     size_t pd_smem = 0;
     if (kind != RRS_HALFSPACE) {
         if (n > 0x7FFFFFFF) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n too large");
-        G = pdap_max_group((int)n, ldx, m);
+        G = pdap_max_group((int)n, ldx, m, d);
         if (G == 0) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n=%lld too large for the selection kernel", (long long)n);
         pd_smem = pdap_smem_bytes((int)n, G, ldx);
     }

@@ -313,7 +313,7 @@ rrs_status rrs_server_submit(rrs_server* S, int64_t dataset_id, const void* Z, i
     if (m > S->max_m || it->second.d > S->max_d || n_queries > S->cap)
         return sfail(RRS_ERR_UNSUPPORTED, "request exceeds the server's slot shape (m=%d, d=%d, nq=%lld)", m,
                      it->second.d, (long long)n_queries);
-    if (kind != RRS_HALFSPACE && pdap_max_group((int)it->second.n, it->second.ldx, m) == 0)
+    if (kind != RRS_HALFSPACE && pdap_max_group((int)it->second.n, it->second.ldx, m, it->second.d) == 0)
         return sfail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
     Request* R = new Request;
     R->id = S->next_id++;
@@ -353,7 +353,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             int G = 0;
             size_t cls = 0;
             if (R->kind != RRS_HALFSPACE) {
-                G = pdap_max_group((int)D.n, D.ldx, R->m);
+                G = pdap_max_group((int)D.n, D.ldx, R->m, D.d);
                 const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
                 for (size_t c : classes)
                     if (need <= c) {
