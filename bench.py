@@ -58,6 +58,7 @@ def parse():
                          "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
                          "grid: the paper's projection-depth timing grid (its Tables 1 and 2)")
     ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
+    ap.add_argument("--sweep", action="store_true", help="c5: serve the stream at 1/8 .. 2x --rate and report each")
     ap.add_argument("--rate", type=float, default=2000.0, help="c5: Poisson arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=3.0, help="c5: arrival window (s)")
     return ap.parse_args()
@@ -437,11 +438,24 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
         results[name] = cnt.cpu().numpy()
         out[name] = entry
     same = bool(np.array_equal(results["tc"], results["fp32"]))
+    # near-tie re-check rate of the tensor-core epilogue: the round-1 directions of a sample of queries,
+    # counted by the debug entry point (points whose fast sign was not trusted / all point-direction pairs)
+    ns = min(nq, 16)
+    U = torch.empty((ns, m, d), dtype=torch.float32, device=dev)
+    for q in range(ns):
+        rrs.rrs_debug_directions(ctx, P.seed, q, 1, m, d, P.alpha, None, U[q])
+    band = torch.zeros(ns, dtype=torch.int64, device=dev)
+    dep = torch.empty((ns, m), dtype=torch.float64, device=dev)
+    rrs.rrs_debug_round_depths(ctx, did, Zd[:ns].contiguous(), ns, rrs.RRS_F32, rrs.RRS_HALFSPACE, m, U,
+                               rrs.RRS_PREC_SPLIT_BF16X3, dep, None, band)
+    torch.cuda.synchronize()
+    recheck = {"rate": float(band.sum().item()) / (ns * m * n), "sample": f"{ns} queries x {m} round-1 directions x n",
+               "rechecks": int(band.sum().item())}
     rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
     return {"workload": WORKLOAD_C3, "queries": nq, "n": n, "d": d, "k": k, "r": r, "tensor_core": out["tc"],
             "fp32_cuda_core": out["fp32"], "speedup_tc_over_fp32": out["fp32"]["ms_per_step"] / out["tc"]["ms_per_step"],
-            "counts_identical": same}
+            "counts_identical": same, "tensor_core_recheck": recheck}
 
 
 def run_c3(args):
@@ -455,7 +469,8 @@ def run_c3(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_C3, "n": h["n"], "d": h["d"], "queries": h["queries"], "k": h["k"],
                        "r": h["r"], "l2": "flushed between timed steps (512 MiB device write)"},
-            **{key: h[key] for key in ("tensor_core", "fp32_cuda_core", "speedup_tc_over_fp32", "counts_identical")}}
+            **{key: h[key] for key in ("tensor_core", "fp32_cuda_core", "speedup_tc_over_fp32", "counts_identical",
+                                       "tensor_core_recheck")}}
     assert h["counts_identical"], "tensor-core and FP32 counts differ"
     print(json.dumps(line), flush=True)
 
@@ -609,49 +624,80 @@ def run_c5(args):
     torch.cuda.synchronize()
 
     # ---- continuous batching ----------------------------------------------------------------
-    srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream, precision=tc)
-    outs, lat, shed, served_q = {}, [], 0, 0
-    inflight = collections.deque()
-    backlog = 0
+    def serve_stream(reqs):
+        srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream, precision=tc)
+        outs, lat, shed, served_q = {}, [], 0, 0
+        inflight = collections.deque()
+        backlog = 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(reqs) or outs:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i].t_arrival <= now:
+                q = reqs[i]
+                nq = q.Z.shape[0]
+                if backlog + nq > backlog_limit:
+                    shed += 1
+                else:
+                    out = np.empty(nq)
+                    rid = rrs.rrs_server_submit(srv, ids[q.dataset], q.Z, nq, rrs.RRS_F32, q.kind, k, r, alpha, i,
+                                                out)
+                    outs[rid] = (q.t_arrival, nq, out)
+                    backlog += nq
+                i += 1
+            if outs:
+                rrs.rrs_server_step(srv)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight.append(ev)
+                if len(inflight) > 2:
+                    inflight.popleft().synchronize()
+            elif i < len(reqs):
+                time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)))
+            for rid in list(outs):
+                if rrs.rrs_server_poll(srv, rid):
+                    ta, nq, _ = outs.pop(rid)
+                    lat.append(time.perf_counter() - t0 - ta)
+                    backlog -= nq
+                    served_q += nq
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rrs.rrs_server_destroy(srv)
+        rrs.rrs_check(ctx, stream)
+        return {"served_requests": len(lat), "shed_requests": shed, "queries": served_q,
+                "value": served_q / wall, "wall_s": wall, **_latency_stats(lat)}
+
+    if args.sweep:
+        # rate sweep on the same resident datasets: the highest rate that sheds nothing and keeps p99
+        # below half the arrival window (the backlog does not grow over the window)
+        sampler = ClockSampler(0)
+        sampler.start()
+        sweep = []
+        for f in (0.125, 0.25, 0.5, 1.0, 2.0):
+            rate = args.rate * f
+            _, rq = workloads.c5(rate=rate, window_s=args.window, scale=args.scale)
+            cb = serve_stream(rq)
+            sweep.append({"rate_req_per_s": rate, "offered_requests": len(rq), **cb})
+        clocks = sampler.stop()
+        stable = [x["rate_req_per_s"] for x in sweep
+                  if x["shed_requests"] == 0 and x.get("p99_ms", 1e30) <= 500.0 * args.window]
+        for did in ids:
+            rrs.rrs_free(ctx, did)
+        rrs.rrs_destroy(ctx)
+        line = {"metric": METRIC, "value": max(x["value"] for x in sweep), "unit": "query-depths/s", "n_gpus": 1,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x3->f32 (halfspace), f32 (projection)", "data": "synthetic",
+                "config": {"workload": WORKLOAD_C5, "window_s": args.window, "scale": args.scale, "slots": max_slots,
+                           "backlog_limit_queries": backlog_limit, "rates": [x["rate_req_per_s"] for x in sweep]},
+                "sweep": sweep, "max_stable_rate_req_per_s": max(stable) if stable else None, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+        return
+
     sampler = ClockSampler(0)
     sampler.start()
-    t0 = time.perf_counter()
-    i = 0
-    while i < len(reqs) or outs:
-        now = time.perf_counter() - t0
-        while i < len(reqs) and reqs[i].t_arrival <= now:
-            q = reqs[i]
-            nq = q.Z.shape[0]
-            if backlog + nq > backlog_limit:
-                shed += 1
-            else:
-                out = np.empty(nq)
-                rid = rrs.rrs_server_submit(srv, ids[q.dataset], q.Z, nq, rrs.RRS_F32, q.kind, k, r, alpha, i, out)
-                outs[rid] = (q.t_arrival, nq, out)
-                backlog += nq
-            i += 1
-        if outs:
-            rrs.rrs_server_step(srv)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-            inflight.append(ev)
-            if len(inflight) > 2:
-                inflight.popleft().synchronize()
-        elif i < len(reqs):
-            time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)))
-        for rid in list(outs):
-            if rrs.rrs_server_poll(srv, rid):
-                ta, nq, _ = outs.pop(rid)
-                lat.append(time.perf_counter() - t0 - ta)
-                backlog -= nq
-                served_q += nq
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    cb = serve_stream(reqs)
     clocks = sampler.stop()
-    rrs.rrs_server_destroy(srv)
-    rrs.rrs_check(ctx, stream)
-    cb = {"served_requests": len(lat), "shed_requests": shed, "queries": served_q,
-          "value": served_q / wall, "wall_s": wall, **_latency_stats(lat)}
+    wall = cb["wall_s"]
 
     # ---- one rrs_depth call per request, arrival order ------------------------------------------
     lat2, shed2, served2 = [], 0, 0
