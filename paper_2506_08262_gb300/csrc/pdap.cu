@@ -477,10 +477,12 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
 
 // G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
 // directions are then held in registers), 0 for any d.
+// kin: optional precomputed keys, G x npad per task in launch order (k_keys), read instead of projecting
 template <int G, int DP4>
 __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err)
+                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err,
+                                                 const float* __restrict__ kin)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ Ctl C;
@@ -564,7 +566,23 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
             }
         };
-        if (G == 4 && DP4 > 0) {
+        if (kin) {
+            // keys formed by k_keys (same arithmetic as the projection below): copy and count
+            const float4* src = reinterpret_cast<const float4*>(kin + (size_t)blockIdx.x * G * npad);
+            for (int e = tid; e < G * npad / 4; e += NTK) {
+                const int g = e / (npad / 4), i = 4 * (e - g * (npad / 4));
+                if (g >= GA) continue;
+                const float4 k4 = src[e];
+                const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    if (i + h < n) {
+                        keys[(size_t)g * npad + i + h] = kv[h];
+                        atomicAdd(&hist[g * NB + bucket_fma(kv[h], sc[g], of[g])], 1u);
+                    }
+                }
+            }
+        } else if (G == 4 && DP4 > 0) {
             // two adjacent lanes per point, each forming the keys of two directions: the row load is
             // coalesced within the warp and each lane holds only two direction vectors
             constexpr int D4 = DP4 > 0 ? DP4 : 4;
@@ -684,12 +702,13 @@ size_t pdap_two_per_sm_limit()
     return 112 * 1024;
 }
 
-int pdap_max_group(int n, int ldx, int m, int d)
+int pdap_max_group(int n, int ldx, int m, int d, bool keys_in)
 {
-    // G in {1, 2, 4}.  For d <= 16 (directions held in registers) the largest G that fits two CTAs
-    // per SM when that is at least 2, else the largest that fits one CTA per SM.  For larger d the
-    // projection pass re-reads X (4 d bytes per point) for every G directions, so the largest G that
-    // fits wins (measured at n = 10,000: d = 50 1.27x, d = 150 1.68x faster with G = 4 than G = 2).
+    // G in {1, 2, 4}: the largest G that fits two CTAs per SM when that is at least 2, else the
+    // largest that fits one CTA per SM.  Exception: for d > 16 with keys formed inside the kernel
+    // the projection pass re-reads X (4 d bytes per point) for every G directions, so there the
+    // largest G that fits wins (measured at n = 10,000: d = 50 1.27x, d = 150 1.68x faster with
+    // G = 4 than G = 2); with keys from k_keys the usual rule holds again.
     const size_t one = pdap_smem_limit(), two = pdap_two_per_sm_limit();
     int g_one = 0, g_two = 0;
     for (int g = 1; g <= MAXG && g <= m; g *= 2) {
@@ -697,34 +716,116 @@ int pdap_max_group(int n, int ldx, int m, int d)
         if (need <= one) g_one = g;
         if (need <= two) g_two = g;
     }
-    if (pdap_dp4_class(d) == 0) return g_one;
+    if (pdap_dp4_class(d) == 0 && !keys_in) return g_one;
     if (g_two >= 2) return g_two;
     return g_one;
 }
 
+// Keys of a block of tasks (G directions each, all of one dataset) for every point, as a tiled FP32
+// GEMM: keys[(t * G + g) * npad + i] = u_{t,g}'x_i, each key one sequential FMA chain over the dims
+// (the selection kernel's own arithmetic for d > 16, and y_z's), so results do not depend on which
+// kernel formed the keys.  CTA tile: 128 points x 64 directions, 256 threads of 8 x 4 outputs, the
+// dims staged 16 at a time in shared memory.
+constexpr int KT_P = 128, KT_D = 64, KT_K = 16;
+
+__global__ void __launch_bounds__(256) k_keys(const TaskDev* __restrict__ tasks, int ntasks, int G,
+                                              const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets,
+                                              const float* __restrict__ U, float* __restrict__ keys, int npad)
+{
+    __shared__ __align__(16) float Xs[KT_K][KT_P + 4];   // [dim][point]
+    __shared__ __align__(16) float Us[KT_K][KT_D];       // [dim][direction]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const DsDev D = dsets[slots[tasks[0].slot].ds];
+    const int n = (int)D.n, ldx = D.ldx, dp4 = (D.d + 3) & ~3;
+    const int i0 = blockIdx.x * KT_P, r0 = blockIdx.y * KT_D;
+    // this thread's staging roles: one point row half (8 dims) and one direction quarter (4 dims)
+    const int lp = tid >> 1, lh = (tid & 1) * 8;
+    const int ld_ = tid >> 2, lq = (tid & 3) * 4;
+    const float* urow = nullptr;
+    {
+        const int r = r0 + ld_, t = r / G, g = r - t * G;
+        if (t < ntasks && g < tasks[t].nj) {
+            const TaskDev T = tasks[t];
+            urow = U + slots[T.slot].uoff + (int64_t)(T.j0 + g) * ldx;
+        }
+    }
+    const float* xrow = (i0 + lp < n) ? D.X32 + (int64_t)(i0 + lp) * ldx : nullptr;
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    for (int k0 = 0; k0 < dp4; k0 += KT_K) {
+        // zero beyond the row (rows are zero-padded to ldx, so the extra terms add exact zeros)
+#pragma unroll
+        for (int h = 0; h < 8; h += 4) {
+            const int l = k0 + lh + h;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (xrow && l + 4 <= ldx) v = *reinterpret_cast<const float4*>(xrow + l);
+            Xs[lh + h][lp] = v.x;
+            Xs[lh + h + 1][lp] = v.y;
+            Xs[lh + h + 2][lp] = v.z;
+            Xs[lh + h + 3][lp] = v.w;
+        }
+        {
+            const int l = k0 + lq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (urow && l + 4 <= ldx) v = *reinterpret_cast<const float4*>(urow + l);
+            Us[lq][ld_] = v.x;
+            Us[lq + 1][ld_] = v.y;
+            Us[lq + 2][ld_] = v.z;
+            Us[lq + 3][ld_] = v.w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KT_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8 + 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Us[kk][ty * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bv[c], av[a], acc[a][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int r = r0 + ty * 4 + c, t = r / G, g = r - t * G;
+        if (t >= ntasks || g >= tasks[t].nj) continue;
+        float* out = keys + (size_t)r * npad + i0 + tx * 8;
+        if (i0 + tx * 8 + 4 <= npad) *reinterpret_cast<float4*>(out) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        if (i0 + tx * 8 + 8 <= npad)
+            *reinterpret_cast<float4*>(out + 4) = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
+    }
+}
+
 template <int G, int DP4>
 static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
-                            const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+                            const float* U, const float* z32, ResDev* res, int* err, const float* kin, cudaStream_t st)
 {
     cudaError_t e = cudaFuncSetAttribute(k_pdap2<G, DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<G, DP4><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err);
+    k_pdap2<G, DP4><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err, kin);
     return cudaGetLastError();
 }
 
 template <int G>
 static cudaError_t launch_g(int dp4, const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots,
-                            const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+                            const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, const float* kin,
+                            cudaStream_t st)
 {
     switch (dp4) {
-    case 4: return launch_t<G, 4>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    case 8: return launch_t<G, 8>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    case 12: return launch_t<G, 12>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    case 16: return launch_t<G, 16>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    default: return launch_t<G, 0>(tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 4: return launch_t<G, 4>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 8: return launch_t<G, 8>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 12: return launch_t<G, 12>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 16: return launch_t<G, 16>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    default: return launch_t<G, 0>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
     }
 }
 
@@ -735,16 +836,33 @@ int pdap_dp4_class(int d)
 }
 
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
-                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st)
+                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
+                        const float* kin)
 {
     if (ntasks <= 0) return cudaSuccess;
     if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
     switch (group) {
-    case 1: return launch_g<1>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    case 2: return launch_g<2>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
-    case 4: return launch_g<4>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, st);
+    case 1: return launch_g<1>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 2: return launch_g<2>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 4: return launch_g<4>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+size_t pdap_keys_bytes(int n, int group, int ntasks)
+{
+    return sizeof(float) * (size_t)ntasks * group * (((size_t)n + 3) & ~(size_t)3);
+}
+
+cudaError_t launch_pdap_keys(const TaskDev* tasks, int ntasks, int group, const SlotDev* slots, const DsDev* ds,
+                             const DsDev& ds_host, const float* U, float* keys, cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    if (ds_host.n < 1 || ds_host.n > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    const int npad = (int)((ds_host.n + 3) & ~3LL);
+    const dim3 grid((unsigned)((ds_host.n + KT_P - 1) / KT_P), (unsigned)((ntasks * group + KT_D - 1) / KT_D));
+    k_keys<<<grid, 256, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad);
+    return cudaGetLastError();
 }
 
 }  // namespace rrs

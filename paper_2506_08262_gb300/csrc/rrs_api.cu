@@ -142,6 +142,8 @@ struct Plan {
     std::vector<std::vector<TaskDev>> pd_tasks;       // one list per (shared-memory class, group, d class)
     std::vector<size_t> pd_smem;                      // bytes of each list's class
     std::vector<int> pd_group, pd_dp4;
+    std::vector<int> pd_keys_ds;                      // d > 16: dataset whose keys k_keys forms first (-1: none)
+    std::vector<int> pd_keys_chunk;                   // tasks per keys launch (bounded by the keys scratch)
     std::vector<int32_t> argmin_list;
     // active prefix lengths per round
     std::vector<int> n_gen, n_hd, n_arg;
@@ -166,7 +168,8 @@ struct Plan {
     TaskDev *d_gen = nullptr, *d_hd = nullptr;
     std::vector<TaskDev*> d_pd;
     int32_t* d_arg = nullptr;
-    float *z32 = nullptr, *poles = nullptr, *U = nullptr;
+    float *z32 = nullptr, *poles = nullptr, *U = nullptr, *keys = nullptr;
+    size_t keys_floats = 0;
     double *z64 = nullptr, *yz = nullptr;
     ResDev* res = nullptr;
 };
@@ -231,9 +234,9 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
     }
     // shared-memory classes for the selection kernel
     const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
-    std::map<std::tuple<size_t, int, int>, int> pd_index;
-    auto pd_list = [&](size_t smem, int group, int dp4) {
-        auto key = std::make_tuple(smem, group, dp4);
+    std::map<std::tuple<size_t, int, int, int>, int> pd_index;
+    auto pd_list = [&](size_t smem, int group, int dp4, int keys_ds) {
+        auto key = std::make_tuple(smem, group, dp4, keys_ds);
         auto it = pd_index.find(key);
         if (it != pd_index.end()) return it->second;
         const int idx = (int)P.pd_tasks.size();
@@ -242,6 +245,8 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
         P.pd_smem.push_back(smem);
         P.pd_group.push_back(group);
         P.pd_dp4.push_back(dp4);
+        P.pd_keys_ds.push_back(keys_ds);
+        P.pd_keys_chunk.push_back(0);
         return idx;
     };
     struct SlotRounds {
@@ -265,15 +270,17 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
                 if (it != P.tune->end()) G = it->second;
             }
             if (G && (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())) G = 0;
-            if (!G) G = pdap_max_group((int)D.n, D.ldx, m, D.d);
+            if (!G) G = pdap_max_group((int)D.n, D.ldx, m, D.d, pdap_dp4_class(D.d) == 0);
             if (G == 0)
                 return fail(RRS_ERR_UNSUPPORTED,
                             "projection depth needs n*4 bytes of shared memory per direction; n=%lld is too large",
                             (long long)D.n);
             const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
+            // d > 16: keys come from a tiled GEMM (one list per dataset, since a GEMM launch reads one X)
+            const int keys_ds = pdap_dp4_class(D.d) == 0 ? dsidx[R.dset] : -1;
             for (size_t c : classes)
                 if (need <= c) {
-                    cls = pd_list(c, G, pdap_dp4_class(D.d));
+                    cls = pd_list(c, G, pdap_dp4_class(D.d), keys_ds);
                     break;
                 }
             if (cls < 0) return fail(RRS_ERR_INTERNAL, "no shared-memory class for n=%lld", (long long)D.n);
@@ -353,6 +360,16 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
     for (auto& g : P.tc) prefix(g.tasks, g.n);
     P.n_pd.resize(P.pd_tasks.size());
     for (size_t c = 0; c < P.pd_tasks.size(); ++c) prefix(P.pd_tasks[c], P.n_pd[c]);
+    // keys scratch: one chunk of the largest keys list at a time, at most KEYS_SCRATCH_BYTES
+    constexpr size_t KEYS_SCRATCH_BYTES = 256u << 20;
+    for (size_t c = 0; c < P.pd_tasks.size(); ++c) {
+        if (P.pd_keys_ds[c] < 0 || P.pd_tasks[c].empty()) continue;
+        const int n = (int)P.ds[P.pd_keys_ds[c]].n;
+        const size_t per = pdap_keys_bytes(n, P.pd_group[c], 1);
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>(P.pd_tasks[c].size(), KEYS_SCRATCH_BYTES / per));
+        P.pd_keys_chunk[c] = chunk;
+        P.keys_floats = std::max(P.keys_floats, pdap_keys_bytes(n, P.pd_group[c], chunk) / sizeof(float));
+    }
     P.n_arg.assign(P.rmax, 0);
     for (int l = 0; l < P.rmax; ++l) {
         int c = 0;
@@ -378,6 +395,7 @@ size_t carve_plan(Plan& P, Carve& C)
     P.U = C.take<float>(P.tot_u);
     P.yz = C.take<double>(P.tot_m);
     P.res = C.take<ResDev>(P.tot_m);
+    P.keys = P.keys_floats ? C.take<float>(P.keys_floats) : nullptr;
     return C.off;
 }
 
@@ -435,13 +453,26 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
             ctx->launches++;
         }
         for (size_t c = 0; c < P.pd_tasks.size(); ++c) {
-            if (P.n_pd[c][l] > 0) {
+            if (P.n_pd[c][l] <= 0) continue;
+            if (P.pd_keys_ds[c] < 0) {
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_dp4[c], P.d_slots,
-                                     P.d_ds, P.U, P.z32, P.res,
-                                     ctx->d_err, st));
+                                     P.d_ds, P.U, P.z32, P.res, ctx->d_err, st));
                 ctx->launches++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
+                continue;
+            }
+            // keys by the tiled GEMM, then the selection on them, one scratch-sized chunk at a time
+            const int total = P.n_pd[c][l], chunk = P.pd_keys_chunk[c];
+            for (int t0 = 0; t0 < total; t0 += chunk) {
+                const int cnt = std::min(chunk, total - t0);
+                StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
+                CUDA_TRY(launch_pdap_keys(P.d_pd[c] + t0, cnt, P.pd_group[c], P.d_slots, P.d_ds, P.ds[P.pd_keys_ds[c]],
+                                          P.U, P.keys, st));
+                CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_dp4[c], P.d_slots,
+                                     P.d_ds, P.U, P.z32, P.res, ctx->d_err, st, P.keys));
+                ctx->launches += 2;
+                ctx->stage_launches[RRS_STAGE_PDAP] += 2;
             }
         }
         if (P.n_arg[l] > 0) {

@@ -104,7 +104,14 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
                            int* err, cudaStream_t st);
 // group: directions per CTA (1, 2 or 4, from pdap_max_group); dp4: pdap_dp4_class(d), shared by every task
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
-                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st);
+                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
+                        const float* kin = nullptr);
+// Keys of ntasks selection tasks (all of one dataset) by a tiled FP32 GEMM into keys
+// (pdap_keys_bytes), for launch_pdap(..., kin = keys) on the same task range; used for d > 16,
+// where forming the keys inside the selection kernel re-reads X for every G directions
+size_t pdap_keys_bytes(int n, int group, int ntasks);
+cudaError_t launch_pdap_keys(const TaskDev* tasks, int ntasks, int group, const SlotDev* slots, const DsDev* ds,
+                             const DsDev& ds_host, const float* U, float* keys, cudaStream_t st);
 int pdap_dp4_class(int d);
 cudaError_t launch_argmin(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
                           const ResDev* res, const float* poles_cur, float* poles_next, int round0,
@@ -129,7 +136,7 @@ cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* c
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx);
 size_t pdap_smem_limit();
-int pdap_max_group(int n, int ldx, int m, int d);   // preferred G (0 if none fits)
+int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // preferred G (0 if none fits)
 
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,

@@ -185,6 +185,15 @@ def test_projection_depth_shapes(ctx, kind, n, d):
 
 
 @pytest.mark.parametrize("kind", [P, AP])
+@pytest.mark.parametrize("n,d", [(3000, 17), (2500, 50), (1200, 150)])
+def test_projection_depth_large_d(ctx, kind, n, d):
+    # d > 16: keys formed by the tiled GEMM and read by the selection kernel
+    X, Z = workloads.gaussian_cloud(n + d, n, d, 6, dtype=np.float32, zscale=0.8)
+    g = gpu_rrs(ctx, X, Z, kind, 240, 3, 0.8, 5)
+    assert_follow(g, X, Z, kind, 240, 3, 0.8, 5)
+
+
+@pytest.mark.parametrize("kind", [P, AP])
 def test_projection_round_depths(ctx, kind):
     X, Z = workloads.gaussian_cloud(9, 3001, 10, 2, dtype=np.float32)
     m = 50
