@@ -112,6 +112,8 @@ struct rrs_server {
     int ds_cap = 0;
     char* d_tab = nullptr;      // per-step tables (tasks, lists, new slots)
     size_t tab_bytes = 0;
+    float* d_keys = nullptr;    // selection keys formed by k_keys for d > 16 (at most KEYS_SCRATCH_BYTES)
+    size_t keys_bytes = 0;
     // host
     std::vector<int32_t> free_slots;
     std::deque<Request*> pending;
@@ -345,7 +347,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
         std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
-        std::map<std::tuple<size_t, int, int>, std::vector<TaskDev>> pd;
+        // selection lists per (shared-memory class, G, d class, dataset row for keys by k_keys or -1)
+        std::map<std::tuple<size_t, int, int, int>, std::vector<TaskDev>> pd;
         std::vector<int32_t> arg;
         const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
         for (Request* R : S->active) {
@@ -353,7 +356,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             int G = 0;
             size_t cls = 0;
             if (R->kind != RRS_HALFSPACE) {
-                G = pdap_max_group((int)D.n, D.ldx, R->m, D.d);
+                G = pdap_max_group((int)D.n, D.ldx, R->m, D.d, pdap_dp4_class(D.d) == 0);
                 const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
                 for (size_t c : classes)
                     if (need <= c) {
@@ -373,7 +376,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 } else if (R->kind == RRS_HALFSPACE) {
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
                 } else {
-                    auto& v = pd[std::make_tuple(cls, G, pdap_dp4_class(D.d))];
+                    const int keys_row = pdap_dp4_class(D.d) == 0 ? row : -1;
+                    auto& v = pd[std::make_tuple(cls, G, pdap_dp4_class(D.d), keys_row)];
                     for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), 0});
                 }
                 arg.push_back(slot);
@@ -395,7 +399,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         const size_t o_gen = put(gen.data(), sizeof(TaskDev) * gen.size());
         const size_t o_hd = put(hd.data(), sizeof(TaskDev) * hd.size());
         const size_t o_arg = put(arg.data(), sizeof(int32_t) * arg.size());
-        std::vector<std::pair<size_t, std::tuple<size_t, int, int>>> o_pd;
+        std::vector<std::pair<size_t, std::tuple<size_t, int, int, int>>> o_pd;
         for (auto& kv : pd) o_pd.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
         std::vector<std::pair<size_t, int>> o_tc;
         for (auto& kv : tc) o_tc.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
@@ -409,15 +413,41 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), S->d_slots, S->d_ds,
                                S->ds_host[to.second], S->d_U, S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err,
                                S->st));
+        size_t extra = 0;
         for (auto& po : o_pd) {
             const auto& key = po.second;
-            S_TRY(launch_pdap((const TaskDev*)(T + po.first), (int)pd[key].size(), std::get<0>(key), std::get<1>(key),
-                              std::get<2>(key), S->d_slots, S->d_ds, S->d_U, S->d_z32, S->d_res, S->ctx->d_err,
-                              S->st));
+            const TaskDev* tl = (const TaskDev*)(T + po.first);
+            const int cnt_all = (int)pd[key].size(), G = std::get<1>(key), krow = std::get<3>(key);
+            if (krow < 0) {
+                S_TRY(launch_pdap(tl, cnt_all, std::get<0>(key), G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
+                                  S->d_z32, S->d_res, S->ctx->d_err, S->st));
+                continue;
+            }
+            // d > 16: keys by the tiled GEMM, then the selection on them, one scratch-sized chunk at a time
+            constexpr size_t KEYS_SCRATCH_BYTES = 256u << 20;
+            const int n = (int)S->ds_host[krow].n;
+            const size_t per = pdap_keys_bytes(n, G, 1);
+            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cnt_all, KEYS_SCRATCH_BYTES / per));
+            const size_t need_b = pdap_keys_bytes(n, G, chunk);
+            if (need_b > S->keys_bytes) {
+                if (S->d_keys) S_TRY(cudaFreeAsync(S->d_keys, S->st));
+                S->d_keys = nullptr;
+                S_TRY(cudaMallocAsync((void**)&S->d_keys, need_b, S->st));
+                S->keys_bytes = need_b;
+            }
+            for (int t0 = 0; t0 < cnt_all; t0 += chunk) {
+                const int cnt = std::min(chunk, cnt_all - t0);
+                S_TRY(launch_pdap_keys(tl + t0, cnt, G, S->d_slots, S->d_ds, S->ds_host[krow], S->d_U, S->d_keys,
+                                       S->st));
+                S_TRY(launch_pdap(tl + t0, cnt, std::get<0>(key), G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
+                                  S->d_z32, S->d_res, S->ctx->d_err, S->st, S->d_keys));
+                extra += 2;
+            }
+            extra--;   // counted once below
         }
         S_TRY(launch_argmin_slotround(S->d_slots, (const int32_t*)(T + o_arg), (int)arg.size(), S->d_U, S->d_res,
                                      S->d_p0, S->d_p1, S->st));
-        S->ctx->launches += 3 + pd.size() + tc.size();
+        S->ctx->launches += 3 + pd.size() + tc.size() + extra;
         // retire requests whose last round just ran
         std::vector<Request*> still;
         for (Request* R : S->active) {
@@ -480,6 +510,7 @@ rrs_status rrs_server_destroy(rrs_server* S)
         delete R;
     }
     if (S->d_tab) cudaFree(S->d_tab);
+    if (S->d_keys) cudaFree(S->d_keys);
     cudaFree(S->arena);
     S->ctx->used -= S->arena_bytes;
     delete S;
