@@ -724,76 +724,72 @@ int pdap_max_group(int n, int ldx, int m, int d, bool keys_in)
 // Keys of a block of tasks (G directions each, all of one dataset) for every point, as a tiled FP32
 // GEMM: keys[(t * G + g) * npad + i] = u_{t,g}'x_i, each key one sequential FMA chain over the dims
 // (the selection kernel's own arithmetic for d > 16, and y_z's), so results do not depend on which
-// kernel formed the keys.  CTA tile: 128 points x 64 directions, 256 threads of 8 x 4 outputs, the
+// kernel formed the keys.  CTA tile: 128 points x 128 directions, 256 threads of 8 x 8 outputs, the
 // dims staged 16 at a time in shared memory.
-constexpr int KT_P = 128, KT_D = 64, KT_K = 16;
+constexpr int KT_P = 128, KT_D = 128, KT_K = 16;
 
 __global__ void __launch_bounds__(256) k_keys(const TaskDev* __restrict__ tasks, int ntasks, int G,
                                               const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets,
                                               const float* __restrict__ U, float* __restrict__ keys, int npad)
 {
     __shared__ __align__(16) float Xs[KT_K][KT_P + 4];   // [dim][point]
-    __shared__ __align__(16) float Us[KT_K][KT_D];       // [dim][direction]
+    __shared__ __align__(16) float Us[KT_K][KT_D + 4];   // [dim][direction]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const DsDev D = dsets[slots[tasks[0].slot].ds];
     const int n = (int)D.n, ldx = D.ldx, dp4 = (D.d + 3) & ~3;
     const int i0 = blockIdx.x * KT_P, r0 = blockIdx.y * KT_D;
-    // this thread's staging roles: one point row half (8 dims) and one direction quarter (4 dims)
-    const int lp = tid >> 1, lh = (tid & 1) * 8;
-    const int ld_ = tid >> 2, lq = (tid & 3) * 4;
+    // staging: thread tid loads 8 dims of point row tid / 2 and 8 dims of direction row tid / 2
+    const int lr = tid >> 1, lh = (tid & 1) * 8;
     const float* urow = nullptr;
     {
-        const int r = r0 + ld_, t = r / G, g = r - t * G;
+        const int r = r0 + lr, t = r / G, g = r - t * G;
         if (t < ntasks && g < tasks[t].nj) {
             const TaskDev T = tasks[t];
             urow = U + slots[T.slot].uoff + (int64_t)(T.j0 + g) * ldx;
         }
     }
-    const float* xrow = (i0 + lp < n) ? D.X32 + (int64_t)(i0 + lp) * ldx : nullptr;
-    float acc[8][4];
+    const float* xrow = (i0 + lr < n) ? D.X32 + (int64_t)(i0 + lr) * ldx : nullptr;
+    float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
     for (int k0 = 0; k0 < dp4; k0 += KT_K) {
         // zero beyond the row (rows are zero-padded to ldx, so the extra terms add exact zeros)
 #pragma unroll
         for (int h = 0; h < 8; h += 4) {
             const int l = k0 + lh + h;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f), w = v;
             if (xrow && l + 4 <= ldx) v = *reinterpret_cast<const float4*>(xrow + l);
-            Xs[lh + h][lp] = v.x;
-            Xs[lh + h + 1][lp] = v.y;
-            Xs[lh + h + 2][lp] = v.z;
-            Xs[lh + h + 3][lp] = v.w;
-        }
-        {
-            const int l = k0 + lq;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (urow && l + 4 <= ldx) v = *reinterpret_cast<const float4*>(urow + l);
-            Us[lq][ld_] = v.x;
-            Us[lq + 1][ld_] = v.y;
-            Us[lq + 2][ld_] = v.z;
-            Us[lq + 3][ld_] = v.w;
+            if (urow && l + 4 <= ldx) w = *reinterpret_cast<const float4*>(urow + l);
+            Xs[lh + h][lr] = v.x;
+            Xs[lh + h + 1][lr] = v.y;
+            Xs[lh + h + 2][lr] = v.z;
+            Xs[lh + h + 3][lr] = v.w;
+            Us[lh + h][lr] = w.x;
+            Us[lh + h + 1][lr] = w.y;
+            Us[lh + h + 2][lr] = w.z;
+            Us[lh + h + 3][lr] = w.w;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < KT_K; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8]);
             const float4 a1 = *reinterpret_cast<const float4*>(&Xs[kk][tx * 8 + 4]);
-            const float4 b = *reinterpret_cast<const float4*>(&Us[kk][ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Us[kk][ty * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Us[kk][ty * 8 + 4]);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[4] = {b.x, b.y, b.z, b.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(bv[c], av[a], acc[a][c]);
+                for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(bv[c], av[a], acc[a][c]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int r = r0 + ty * 4 + c, t = r / G, g = r - t * G;
+    for (int c = 0; c < 8; ++c) {
+        const int r = r0 + ty * 8 + c, t = r / G, g = r - t * G;
         if (t >= ntasks || g >= tasks[t].nj) continue;
         float* out = keys + (size_t)r * npad + i0 + tx * 8;
         if (i0 + tx * 8 + 4 <= npad) *reinterpret_cast<float4*>(out) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
