@@ -269,6 +269,21 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     assert np.all(g["count"] >= 0)
 
 
+@pytest.mark.parametrize("kind", [P, AP])
+def test_projection_depth_at_the_largest_n(ctx, kind):
+    # one direction per CTA with its keys in shared memory: n = 55,000 is near the 227 KB limit;
+    # a little beyond it the call is refused (no partial result, the context keeps working)
+    X, Z = workloads.gaussian_cloud(77, 55_000, 4, 3, dtype=np.float32)
+    g = gpu_rrs(ctx, X, Z, kind, 30, 2, 0.7, 2)
+    assert_follow(g, X, Z, kind, 30, 2, 0.7, 2)
+    Xb, Zb = workloads.gaussian_cloud(78, 60_000, 4, 2, dtype=np.float32)
+    with pytest.raises(rrs.RRSError) as e:
+        gpu_rrs(ctx, Xb, Zb, kind, 30, 2, 0.7, 2)
+    assert e.value.status == rrs.RRS_ERR_UNSUPPORTED
+    g2 = gpu_rrs(ctx, X[:500], Z, kind, 30, 2, 0.7, 2)
+    assert np.all((g2["depth"] >= 0) & (g2["depth"] <= 1))
+
+
 def test_zero_queries_is_a_no_op(ctx):
     X = np.ones((4, 2), np.float32)
     did = rrs.rrs_register_dataset(ctx.handle, X, 4, 2, rrs.RRS_F32, False)
