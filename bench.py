@@ -59,6 +59,8 @@ def parse():
                          "grid: the paper's projection-depth timing grid (its Tables 1 and 2)")
     ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
     ap.add_argument("--sweep", action="store_true", help="c5: serve the stream at 1/8 .. 2x --rate and report each")
+    ap.add_argument("--grid-d", type=int, nargs="*", default=None, help="grid: only these dimensions")
+    ap.add_argument("--grid-k", type=int, nargs="*", default=None, help="grid: only these direction counts (r = 1)")
     ap.add_argument("--rate", type=float, default=2000.0, help="c5: Poisson arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=3.0, help="c5: arrival window (s)")
     return ap.parse_args()
@@ -794,11 +796,15 @@ def run_grid(args):
         return min(x.elapsed_time(y) for x, y in evs)
 
     for di, d in enumerate(PAPER_GRID_D):
+        if args.grid_d and d not in args.grid_d:
+            continue
         X, Z = workloads.toeplitz_gaussian(1000 + d, n, d, batch)
         did = rrs.rrs_register_dataset(ctx, torch.from_numpy(X).to(dev), n, d, rrs.RRS_F32, True)
         Zd = torch.from_numpy(Z).to(dev)
         cells = [(k, 1, PAPER_TABLE1[k][di]) for k in sorted(PAPER_TABLE1)]
         cells += [(250_000, r, PAPER_TABLE2[r][di]) for r in sorted(PAPER_TABLE2)]
+        if args.grid_k:
+            cells = [c for c in cells if c[0] in args.grid_k and c[1] == 1]
         for k, r, paper_s in cells:
             reps = 2 if k >= 250_000 else (3 if k >= 100_000 else 5)
             nb = 8 if k >= 250_000 else batch   # bounded run time: 8 points per call at k = 250,000
