@@ -11,19 +11,21 @@
 // dot product (about twice FP32 precision) and, when even that is too close
 // to call, by the exact FP64 sign test, so the counts are exact.
 //
-// CTA layout (576 threads): warp 0 streams point tiles with TMA into a
+// CTA layout (640 threads): warp 0 streams point tiles with TMA into a
 // 2-stage ring, warp 1 owns tensor memory and issues the MMAs, warps 2-17 read
 // the accumulator (one accumulator row per TMEM lane, four warps per lane
-// quarter, each taking one 32-column chunk of every tile) and count.  The 128
+// quarter, each taking one 32-column chunk of every tile) and count, and
+// warps 18-19 settle near ties handed to them by the counting warps.  The 128
 // rows of a CTA are consecutive (query, direction) pairs of one request, so
 // one tile may hold several queries.  Tiles are 256 points wide for a K
 // extent of 64 (four accumulator buffers of 128 columns otherwise); two
 // 256-column accumulator buffers let the MMAs of one tile overlap the
 // epilogue of the previous one.  Per chunk the epilogue packs
 // the sign bits of t and of (b - |t|) into bit words (three instructions per
-// column); columns inside the band go to a per-warp queue that is settled 32
-// at a time, one candidate per lane, so the rare slow test never serialises a
-// warp on one point.
+// column); columns inside the band go to a per-warp queue.  Each full batch
+// of 32 is handed to the settle warps through a small ring in shared memory
+// (settled inline when every slot is taken), so the slow test, one candidate
+// per lane, stays off the path that frees the accumulator buffers.
 // Every wait on an mbarrier is bounded; on timeout the CTA flags ERR_TIMEOUT
 // and winds down.
 #include <cuda.h>
@@ -51,7 +53,9 @@ constexpr int STAGES = 4;                    // largest TMA ring
 constexpr int MAXACC = 4;                    // accumulator buffers: 512 TMEM columns / BN
 constexpr int QCAP = 64;                     // near-tie queue entries per epilogue warp
 constexpr int NEPI = 16;                     // epilogue warps: four per TMEM lane quarter
-constexpr int NTHREADS = 64 + 32 * NEPI;
+constexpr int NSET = 2;                      // settle warps
+constexpr int NSLOT = 8;                     // batches of 32 near ties in flight to the settle warps
+constexpr int NTHREADS = 64 + 32 * (NEPI + NSET);
 
 __host__ __device__ constexpr int plane_bytes_rows(int rows) { return rows * 128; }   // one 64-wide K chunk
 
@@ -125,7 +129,10 @@ struct TcShared {
     int abort;
     int mma_tiles;   // tiles whose operands the MMA issuer has consumed
     unsigned zmax_bits;
+    int sq_state[NSLOT];   // settle ring slots: SQ_FREE, SQ_FILLING, SQ_FULL, SQ_SETTLING
+    int epi_done;          // counting warps that have handed off their last batch
 };
+enum { SQ_FREE = 0, SQ_FILLING = 1, SQ_FULL = 2, SQ_SETTLING = 3 };
 
 // One accumulator row of the CTA: a (query, direction) pair.
 struct RowInfo {
@@ -193,6 +200,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __shared__ __align__(16) float bcol[NEPI][32 * CPW];      // per-column band bound of the warp's chunks
     __shared__ uint32_t qpt[NEPI][QCAP];                      // candidate queue: point index
     __shared__ uint8_t qrow[NEPI][QCAP];                      //                  accumulator row
+    __shared__ uint32_t sq_pt[NSLOT][32];                     // settle ring: point index
+    __shared__ uint8_t sq_row[NSLOT][32];                     //              accumulator row
     __shared__ int cand_lt[BM], cand_gt[BM];                  // exact verdicts on candidates, per row
     __shared__ uint32_t partial_lt[NEPI][32], partial_gt[NEPI][32];
 
@@ -206,7 +215,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     // ---- rows: T covers rows j0 .. j0+nj-1 of its request's (query, direction) sequence,
     //      m directions per query, starting at query slot T.slot -------------------------
-    if (threadIdx.x == 0) sh.zmax_bits = 0u;
+    if (threadIdx.x == 0) {
+        sh.zmax_bits = 0u;
+        for (int i = 0; i < NSLOT; ++i) sh.sq_state[i] = SQ_FREE;
+        sh.epi_done = 0;
+    }
     __syncthreads();
     if (threadIdx.x < BM) {
         const int r = threadIdx.x;
@@ -295,6 +308,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = sh.tmem_base;
 
+    // exact verdicts on near ties: lane k of the calling warp takes entry k of (pts, rws)
+    const double* X64 = D.X64;
+    auto settle = [&](const uint32_t* pts, const uint8_t* rws, int cnt) {
+        __syncwarp();
+        if (lane < cnt) {
+            const int64_t i = pts[lane];
+            const int r = rws[lane];
+            const RowInfo& R = rows[r];
+            const float* ur = U + R.uoff;
+            int sgn;
+            if (X64) {
+                sgn = rrsdev::exact_sign<double>(ur, 1, X64 + i * d, z64 + R.zoff64, d, err);
+            } else {
+                const float* xr = D.X32 + i * ldx;
+                const float bnd = ffcoef * (D.xnorm[i] + R.zn) + (float)(d + 2) * 0x1p-140f;
+                sgn = ff_sign(ur, xr, ldx, R.yh, R.yl, bnd);
+                if (sgn == 0) sgn = rrsdev::exact_sign<float>(ur, 1, xr, z64 + R.zoff64, d, err);
+            }
+            if (sgn < 0) atomicAdd(&cand_lt[r], 1);
+            else if (sgn > 0) atomicAdd(&cand_gt[r], 1);
+            if (band_out) atomicAdd((unsigned long long*)&band_out[R.slot], 1ull);
+        }
+        __syncwarp();
+    };
+
     if (warp == 0) {
         // ---- TMA producer ------------------------------------------------------------------
         if (lane == 0) {
@@ -366,44 +404,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_wait(&sh.acc_full[t % NACC], (t / NACC) & 1, err, false);
             }
         }
-    } else {
+    } else if (warp < 2 + NEPI) {
         // ---- epilogue: one accumulator row (direction) per thread ---------------------------
         // Four warps share each TMEM lane quarter; warp e takes the 32-column chunk e / 4 of
         // every tile.  Per column the sign bits of t and of (bound - |t|) are shifted into bit
         // words (one add and two funnel shifts); the few columns inside the band go to a
-        // per-warp queue that is settled 32 at a time, one candidate per lane.
+        // per-warp queue whose batches of 32 go to the settle warps.
         const int e = warp - 2;                 // 0..NEPI-1
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int cw = e >> 2;                  // column chunk of each tile
         const int row = q * 32 + lane;          // accumulator row = TMEM lane
         const bool live = row < T.nj;
         const float gz = gamma * __uint_as_float(sh.zmax_bits);
-        const double* X64 = D.X64;
         uint32_t lt = 0, gt = 0;                // n < 2^31
         int qn = 0;                             // queue fill (warp-uniform)
 
-        // settle queue entries [b0, b0 + cnt): lane k takes entry b0 + k
-        auto settle = [&](int b0, int cnt) {
-            __syncwarp();
-            if (lane < cnt) {
-                const int64_t i = qpt[e][b0 + lane];
-                const int r = qrow[e][b0 + lane];
-                const RowInfo& R = rows[r];
-                const float* ur = U + R.uoff;
-                int sgn;
-                if (X64) {
-                    sgn = rrsdev::exact_sign<double>(ur, 1, X64 + i * d, z64 + R.zoff64, d, err);
-                } else {
-                    const float* xr = D.X32 + i * ldx;
-                    const float bnd = ffcoef * (D.xnorm[i] + R.zn) + (float)(d + 2) * 0x1p-140f;
-                    sgn = ff_sign(ur, xr, ldx, R.yh, R.yl, bnd);
-                    if (sgn == 0) sgn = rrsdev::exact_sign<float>(ur, 1, xr, z64 + R.zoff64, d, err);
+        // hand queue entries [b0, b0 + 32) to a free slot of the settle ring, or settle them here
+        auto hand_off = [&](int b0) {
+            __syncwarp();   // the entries were appended by several lanes
+            int s = -1;
+            if (lane == 0) {
+                for (int k = 0; k < NSLOT; ++k) {
+                    const int i = (e + k) & (NSLOT - 1);
+                    if (*(volatile int*)&sh.sq_state[i] == SQ_FREE &&
+                        atomicCAS(&sh.sq_state[i], SQ_FREE, SQ_FILLING) == SQ_FREE) {
+                        s = i;
+                        break;
+                    }
                 }
-                if (sgn < 0) atomicAdd(&cand_lt[r], 1);
-                else if (sgn > 0) atomicAdd(&cand_gt[r], 1);
-                if (band_out) atomicAdd((unsigned long long*)&band_out[R.slot], 1ull);
             }
+            s = __shfl_sync(0xFFFFFFFFu, s, 0);
+            if (s < 0) {
+                settle(&qpt[e][b0], &qrow[e][b0], 32);
+                return;
+            }
+            sq_pt[s][lane] = qpt[e][b0 + lane];
+            sq_row[s][lane] = qrow[e][b0 + lane];
             __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicExch(&sh.sq_state[s], SQ_FULL);
+            }
         };
 
         // this lane's column in chunk j of tile t is t * BN + (cw * CPW + j) * 32 + lane; the
@@ -489,7 +530,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                         qn += __popc(bal);
                         if (qn >= 32) {
-                            settle(qn - 32, 32);
+                            hand_off(qn - 32);
                             qn -= 32;
                         }
                         bal = __ballot_sync(0xFFFFFFFFu, cm != 0u);
@@ -506,10 +547,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             xrem -= BN;
             crem -= BN;
         }
-        if (!aborted && qn > 0) settle(0, qn);
+        if (!aborted && qn > 0) settle(&qpt[e][0], &qrow[e][0], qn);
         // the four warps of a lane quarter each counted a quarter of the columns
         partial_lt[e][lane] = lt;
         partial_gt[e][lane] = gt;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicAdd(&sh.epi_done, 1);   // every batch of this warp is in the ring by now
+        }
+    } else {
+        // ---- settle warps: take full ring slots until the counting warps are done ----------
+        // The wait is bounded by progress: it gives up only when the MMA issuer has not moved
+        // for 2e9 cycles while batches may still come.
+        long long t0 = clock64();
+        int seen = -1;
+        for (;;) {
+            int s = -1, fin = 0;
+            if (lane == 0) {
+                for (int i = 0; i < NSLOT; ++i) {
+                    if (*(volatile int*)&sh.sq_state[i] == SQ_FULL &&
+                        atomicCAS(&sh.sq_state[i], SQ_FULL, SQ_SETTLING) == SQ_FULL) {
+                        s = i;
+                        break;
+                    }
+                }
+                if (s >= 0) {
+                    __threadfence_block();
+                } else if (*(volatile int*)&sh.abort) {
+                    fin = 1;
+                } else if (*(volatile int*)&sh.epi_done == NEPI) {
+                    __threadfence_block();
+                    fin = 1;   // no slot is FILLING any more; a FULL one is taken next pass
+                    for (int i = 0; i < NSLOT; ++i)
+                        if (*(volatile int*)&sh.sq_state[i] == SQ_FULL) fin = 0;
+                } else {
+                    const int mt = *(volatile int*)&sh.mma_tiles;
+                    const long long now = clock64();
+                    if (mt != seen) {
+                        seen = mt;
+                        t0 = now;
+                    } else if (now - t0 > 2000000000LL) {
+                        atomicOr(err, ERR_TIMEOUT);
+                        sh.abort = 1;
+                        fin = 1;
+                    }
+                }
+            }
+            s = __shfl_sync(0xFFFFFFFFu, s, 0);
+            fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
+            if (s >= 0) {
+                settle(sq_pt[s], sq_row[s], 32);
+                if (lane == 0) {
+                    __threadfence_block();
+                    atomicExch(&sh.sq_state[s], SQ_FREE);
+                }
+                continue;
+            }
+            if (fin) break;
+            __nanosleep(256);
+        }
     }
     tc_fence_before();
     __syncthreads();
