@@ -41,6 +41,10 @@ WORKLOAD = ("projection + asymmetric projection depth, d=10, n=10000 (95% N(0,I)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant kernel, from a
+# single-pass ncu capture of the same launch shape on a GB300; reported only for that shape.
+TRAFFIC_PDAP_C2 = 3.55e6     # k_pdap2<2,12>, 50,000 directions x 10,000 points, d = 10
+TRAFFIC_HD_TC_C3 = 287.7e6   # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -339,7 +343,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(Zh.numel() * 4 * len(kinds)),
                 "d2h_bytes_per_step": int(nq * 8 * len(kinds))},
         "roofline": {"bound": "alu", "kernel": "k_pdap", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_PDAP_C2 if args.nq == 0 else None,
                      "peak_source": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz (recipe unit counts and max clock)",
                      "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms},
         "stage_ms_per_step": {k2: v[0] / args.steps for k2, v in prof.items() if v[1]},
@@ -427,7 +431,8 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
             flops = 6.0 * d * elems_per_launch   # three BF16 products of d terms per point-direction pair
             achieved = flops / (avg_ms / 1000) / 1e12
             entry["roofline"] = {"bound": "tensor", "kernel": "k_hd_tc", "achieved": achieved, "peak": bf16_peak,
-                                 "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None,
+                                 "unit": "TFLOP/s", "frac": achieved / bf16_peak,
+                                 "traffic": TRAFFIC_HD_TC_C3 if nq == 10_000 else None,
                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
                                  "flops_per_launch": flops}
         else:
