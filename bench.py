@@ -45,6 +45,10 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # single-pass ncu capture of the same launch shape on a GB300; reported only for that shape.
 TRAFFIC_PDAP_C2 = 3.55e6     # k_pdap2<2,12>, 50,000 directions x 10,000 points, d = 10
 TRAFFIC_HD_TC_C3 = 287.7e6   # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50
+# warp instructions the selection kernel executes per (point, direction) element at d = 10, n = 10,000
+# (ncu smsp__inst_executed.sum over one launch / its elements): the work actually done, every pass counted
+WARP_INSTR_PER_ELEMENT_PDAP_C2 = 1.92
+ISSUE_PER_SM_PER_CLK = 4     # one warp instruction per clock on each of the four SM sub-partitions
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -220,6 +224,18 @@ def alu_ops_per_element(kind: int, d: int) -> int:
     return d + 2 * 3 + (2 if kind == workloads.ASYM_PROJECTION else 0)
 
 
+def executed_work(captured_shape: bool, elements_per_launch: float, avg_launch_ms: float):
+    """The selection kernel's executed instructions (all passes: projection, histograms, gathers, exact
+    ranks) against the SM issue peak, for the launch shape whose instruction count was measured."""
+    if not captured_shape:
+        return None
+    instr_per_s = elements_per_launch * WARP_INSTR_PER_ELEMENT_PDAP_C2 / (avg_launch_ms / 1000)
+    peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * SM_MAX_MHZ_NOMINAL * 1e6
+    return {"warp_instr_per_element": WARP_INSTR_PER_ELEMENT_PDAP_C2, "achieved_warp_instr_per_s": instr_per_s,
+            "peak_warp_instr_per_s": peak, "frac": instr_per_s / peak,
+            "source": "instructions per element from ncu smsp__inst_executed.sum; issue peak 152 SMs x 4 x 2070 MHz"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -345,7 +361,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_pdap", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                      "frac": achieved / peak, "traffic": TRAFFIC_PDAP_C2 if args.nq == 0 else None,
                      "peak_source": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz (recipe unit counts and max clock)",
-                     "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms},
+                     "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms,
+                     "executed": executed_work(args.nq == 0, nq * r * m * n * len(kinds) / launches_per_step,
+                                               avg_launch_ms)},
         "stage_ms_per_step": {k2: v[0] / args.steps for k2, v in prof.items() if v[1]},
         "stage_share": stage_share,
         "clocks": clocks,
