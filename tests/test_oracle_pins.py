@@ -339,6 +339,33 @@ def test_rrs_gaussian_limits():
     np.testing.assert_allclose(h, 1 - norm.cdf(radii), atol=tol)
 
 
+def test_rrs_one_round_is_simple_random_search():
+    # Alg. S2 (simple random search): with r = 1 the search is the minimum of the univariate depth over k
+    # directions drawn uniformly on the sphere, the lowest index winning ties.  The univariate depths here are
+    # written out with numpy (median, unscaled MAD, halfspace counts), independently of the oracle's own.
+    X, Z = workloads.gaussian_cloud(16, 301, 4, 5)
+    k, seed = 64, 11
+    for kind in (H, P):
+        out = oracle.rrs(X, Z, kind, k, 1, 0.5, seed)
+        for q in range(Z.shape[0]):
+            U = oracle.directions(seed, q, 0, k, X.shape[1], 0.5).astype(np.float64)
+            y = X @ U.T                                  # n x k projections
+            yz = U @ Z[q]
+            if kind == H:
+                le = np.sum(y <= yz, axis=0)
+                ge = np.sum(y >= yz, axis=0)
+                c = np.minimum(le, ge)
+                assert out["count"][q] == min(c.min(), X.shape[0])
+                want_best = int(np.argmin(c)) if c.min() < X.shape[0] else -1
+                assert out["best"][q] == want_best
+            else:
+                med = np.median(y, axis=0)
+                mad = np.median(np.abs(y - med), axis=0)
+                dj = 1.0 / (1.0 + np.abs(yz - med) / mad)
+                np.testing.assert_allclose(out["depth"][q], min(dj.min(), 1.0), rtol=1e-12)
+                assert out["best"][q] == int(np.argmin(dj))
+
+
 def test_rrs_follow_mode_replays_own_choices():
     X, Z = workloads.gaussian_cloud(14, 400, 4, 6, dtype=np.float32)
     own = oracle.rrs(X, Z, P, 120, 6, 0.7, 3, rounds=True)
