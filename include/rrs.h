@@ -104,6 +104,11 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id);
  *   depth.  Halfspace counts are exact either way: every point whose fast
  *   projection lies in the near-tie band |u'x - u'z| <= b is re-checked
  *   with an exact FP64 sign test.
+ *   Projection depths take the exact median / MAD / MAD_+ of the FP32
+ *   projections; while n FP32 keys per direction fit in shared memory they
+ *   are held there, beyond that (n above ~55,000) every selection pass
+ *   recomputes them from X with the same arithmetic, so results do not depend
+ *   on which form ran.  n is limited to 2^31 - 1 for projection depths.
  * Outputs (each n_queries long, or n_queries*r for round_choice_out):
  *   depth_out[q]   final depth D_min (double).                      required
  *   count_out[q]   halfspace: min(#<=, #>=) at D_min, else -1.        optional
@@ -174,7 +179,9 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
  * fastest is cached in the context; later rrs_depth / rrs_depth_batched calls
  * with the same (n, d, m) use it.  Without tuning a shared-memory heuristic
  * decides.  Results never depend on the choice.  *choice_out (optional)
- * receives it (0 for halfspace depth, which has nothing to tune).
+ * receives it (0 for halfspace depth, which has nothing to tune, and 0 when
+ * no choice keeps the keys in shared memory: the kernel then recomputes them
+ * at every pass with a fixed shape).
  * Synchronous.  Errors: INVALID_ARG, NOT_FOUND, CUDA.
  */
 rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,

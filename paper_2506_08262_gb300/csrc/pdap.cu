@@ -3,8 +3,10 @@
 // MAD_+) of the FP32 keys, depth in FP64 from those few values.
 //
 // One CTA handles G <= 4 directions of one query with the G*n keys resident in
-// shared memory.  The whole CTA projects (pass A: every point on the G
-// directions, keys stored, each added to a 2048-bucket histogram over
+// shared memory, or, when n is beyond what shared memory holds, G = 2
+// directions whose keys are recomputed from X (same arithmetic, so the same
+// values) at every pass over them.  The whole CTA projects (pass A: every
+// point on the G directions, keys stored, each added to a 2048-bucket histogram over
 // u'c +- 5 sigma_u, bucket = monotone FP32 map of the key).  Then the CTA
 // splits into G groups of (CTA threads)/G, one per direction, each synchronising
 // on its own named barrier, so the directions never wait for one another:
@@ -292,22 +294,64 @@ __device__ __forceinline__ float key_halves(const float* u, const float* x)
     return __fadd_rn(p0, p1);
 }
 
-// Exact median / MAD / MAD_+ of each live direction's keys (after the projection
-// pass) and the depth: group g of cta_threads<G>() / G threads handles direction g alone.
-template <int G>
-__device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned* hist, float* buf, int n, int npad,
-                                            bool ap, const DsDev& D, int GA, int64_t roff, ResDev* __restrict__ res,
-                                            int* err)
+// One direction's keys held in shared memory.
+struct KeysResident {
+    const float* y;
+    __device__ __forceinline__ float get(int i) const { return y[i]; }
+    __device__ __forceinline__ float4 get4(int i) const { return *reinterpret_cast<const float4*>(y + i); }
+};
+
+// One direction's keys recomputed from the FP32 rows of X with the projection pass's arithmetic
+// (two half chains for d <= 16, one sequential FMA chain otherwise), so every pass sees the values
+// a resident key would hold.  u: the direction in shared memory, dp4 floats (zero padded).
+template <int DP4>
+struct KeysRecomputed {
+    const float* X;
+    const float* u;
+    int ldx, dp4;
+    __device__ __forceinline__ float get(int i) const
+    {
+        const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)i * ldx);
+        if (DP4 > 0) {
+            constexpr int D4 = DP4 > 0 ? DP4 : 4;
+            float xv[D4], uv[D4];
+#pragma unroll
+            for (int c = 0; c < D4 / 4; ++c) {
+                const float4 t4 = xr[c];
+                const float4 u4 = *reinterpret_cast<const float4*>(u + 4 * c);
+                xv[4 * c] = t4.x;
+                xv[4 * c + 1] = t4.y;
+                xv[4 * c + 2] = t4.z;
+                xv[4 * c + 3] = t4.w;
+                uv[4 * c] = u4.x;
+                uv[4 * c + 1] = u4.y;
+                uv[4 * c + 2] = u4.z;
+                uv[4 * c + 3] = u4.w;
+            }
+            return key_halves<D4>(uv, xv);
+        }
+        float acc = 0.f;
+        for (int l = 0; l < dp4; l += 4) {
+            const float4 x = xr[l >> 2];
+            const float4 w = *reinterpret_cast<const float4*>(u + l);
+            acc = fmaf(w.x, x.x, acc);
+            acc = fmaf(w.y, x.y, acc);
+            acc = fmaf(w.z, x.z, acc);
+            acc = fmaf(w.w, x.w, acc);
+        }
+        return acc;
+    }
+    __device__ __forceinline__ float4 get4(int i) const { return make_float4(get(i), get(i + 1), get(i + 2), get(i + 3)); }
+};
+
+// Exact median / MAD / MAD_+ of one direction's keys y (after the projection pass) and the
+// depth, by its group q of GS threads.
+template <int GS, class K>
+__device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C, unsigned* H, float* B0, int n,
+                                           bool ap, const DsDev& D, int64_t roff, ResDev* __restrict__ res, int* err)
 {
-    constexpr int GS = cta_threads<G>() / G;   // threads per direction group
-    const int tid = threadIdx.x;
-    const Grp<GS> q{tid / GS, tid % GS};
     const int g = q.g;
-    if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
-    const float* y = keys + (size_t)g * npad;
-    unsigned* H = hist + g * NB;
-    float* B0 = buf + (size_t)(2 * g) * CAP;   // median run; FB_CAP = 2 * CAP for the fallback
-    float* B1 = B0 + CAP;                      // MAD_+ guess run (D_AP) or MAD run (D_P)
+    float* B1 = B0 + CAP;                      // MAD_+ guess run (D_AP) or MAD run (D_P); B0 holds the median run
     const float sc = C.sc_y[g], of = C.off_y[g];
     const int k1 = (n - 1) / 2, k2 = n / 2;
     const int n4 = n & ~3;
@@ -352,13 +396,13 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
             }
         };
         for (int i = 4 * q.t; i < n4; i += 4 * GS) {
-            const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+            const float4 y4 = y.get4(i);
             gather(y4.x);
             gather(y4.y);
             gather(y4.z);
             gather(y4.w);
         }
-        for (int i = n4 + q.t; i < n; i += GS) gather(y[i]);
+        for (int i = n4 + q.t; i < n; i += GS) gather(y.get(i));
         q.sync();
         gpick(q, B0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2);
         if (ap) {
@@ -389,13 +433,13 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
             for (int b = q.t; b < NB / 4; b += GS) reinterpret_cast<uint4*>(H)[b] = make_uint4(0u, 0u, 0u, 0u);
             q.sync();
             for (int i = 4 * q.t; i < n4; i += 4 * GS) {
-                const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+                const float4 y4 = y.get4(i);
                 atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.x, m)), scd, 0.0f)], 1u);
                 atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.y, m)), scd, 0.0f)], 1u);
                 atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.z, m)), scd, 0.0f)], 1u);
                 atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.w, m)), scd, 0.0f)], 1u);
             }
-            for (int i = n4 + q.t; i < n; i += GS) atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y[i], m)), scd, 0.0f)], 1u);
+            for (int i = n4 + q.t; i < n; i += GS) atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y.get(i), m)), scd, 0.0f)], 1u);
             q.sync();
             int da, dca, db, dcb;
             gfind(q, H, k1, k2, C, da, dca, db, dcb);
@@ -418,13 +462,13 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
                     }
                 };
                 for (int i = 4 * q.t; i < n4; i += 4 * GS) {
-                    const float4 y4 = *reinterpret_cast<const float4*>(y + i);
+                    const float4 y4 = y.get4(i);
                     gd(y4.x);
                     gd(y4.y);
                     gd(y4.z);
                     gd(y4.w);
                 }
-                for (int i = n4 + q.t; i < n; i += GS) gd(y[i]);
+                for (int i = n4 + q.t; i < n; i += GS) gd(y.get(i));
                 q.sync();
                 gpick(q, B1, cntd, k1 - dca, k2 - dca, C, p1, p2);
             }
@@ -435,26 +479,27 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
     if (fb) {
         float kl = FLT_MAX, kh = -FLT_MAX;
         for (int i = q.t; i < n; i += GS) {
-            kl = fminf(kl, y[i]);
-            kh = fmaxf(kh, y[i]);
+            const float v = y.get(i);
+            kl = fminf(kl, v);
+            kh = fmaxf(kh, v);
         }
         gminmax(q, kl, kh, C, kl, kh);
         unsigned* HF = H;
         float* BF = B0;   // FB_CAP floats: B0 and B1
-        if (fb == 1) gselect(q, [&](int i) { return y[i]; }, n, k1, k2, kl, kh, HF, BF, C, m1, m2, err);
+        if (fb == 1) gselect(q, [&](int i) { return y.get(i); }, n, k1, k2, kl, kh, HF, BF, C, m1, m2, err);
         if (ap) {
             int c = 0;
-            for (int i = q.t; i < n; i += GS) c += (y[i] <= m1);
+            for (int i = q.t; i < n; i += GS) c += (y.get(i) <= m1);
             const int nle = gsum(q, c, C);
             npos = n - nle;
             p1 = p2 = m1;
             if (npos > 0)
-                gselect(q, [&](int i) { return y[i]; }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, HF, BF, C,
+                gselect(q, [&](int i) { return y.get(i); }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, HF, BF, C,
                         p1, p2, err);
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
             const float dmax = fmaxf(fabsf(__fsub_rn(kl, m)), fabsf(__fsub_rn(kh, m)));
-            gselect(q, [&](int i) { return fabsf(__fsub_rn(y[i], m)); }, n, k1, k2, 0.0f, dmax, HF, BF, C, p1, p2,
+            gselect(q, [&](int i) { return fabsf(__fsub_rn(y.get(i), m)); }, n, k1, k2, 0.0f, dmax, HF, BF, C, p1, p2,
                     err);
         }
     }
@@ -475,10 +520,34 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, unsigned*
     }
 }
 
+// Every live direction of the CTA: group g of cta_threads<G>() / G threads handles direction g alone,
+// on its resident keys or (STREAM) on keys recomputed from X.
+template <int G, int DP4, bool STREAM>
+__device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const float* uS, unsigned* hist, float* buf,
+                                            int n, int npad, bool ap, const DsDev& D, int GA, int64_t roff,
+                                            ResDev* __restrict__ res, int* err)
+{
+    constexpr int GS = cta_threads<G>() / G;   // threads per direction group
+    const int tid = threadIdx.x;
+    const Grp<GS> q{tid / GS, tid % GS};
+    const int g = q.g;
+    if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
+    unsigned* H = hist + g * NB;
+    float* B0 = buf + (size_t)(2 * g) * CAP;   // two gather runs; FB_CAP = 2 * CAP for the fallback
+    if (STREAM) {
+        const KeysRecomputed<DP4> y{D.X32, uS + (size_t)g * D.ldx, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
+        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+    } else {
+        const KeysResident y{keys + (size_t)g * npad};
+        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+    }
+}
+
 // G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
-// directions are then held in registers), 0 for any d.
+// directions are then held in registers), 0 for any d; STREAM: no keys in shared
+// memory, every pass recomputes them from X.
 // kin: optional precomputed keys, G x npad per task in launch order (k_keys), read instead of projecting
-template <int G, int DP4>
+template <int G, int DP4, bool STREAM>
 __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
                                                  const float* __restrict__ z32, ResDev* __restrict__ res, int* err,
@@ -493,8 +562,8 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     const bool ap = (S.kind == 2);
     const int tid = threadIdx.x;
     const int npad = (n + 3) & ~3;
-    float* keys = sm;                                          // G x npad
-    float* uS = keys + (size_t)G * npad;                       // G x ldx
+    float* keys = sm;                                          // G x npad (none when STREAM)
+    float* uS = keys + (STREAM ? (size_t)0 : (size_t)G * npad);   // G x ldx
     unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
     float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
 
@@ -562,11 +631,11 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
         auto emit = [&](int i, const float (&acc)[G]) {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                keys[(size_t)g * npad + i] = acc[g];
+                if (!STREAM) keys[(size_t)g * npad + i] = acc[g];
                 atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
             }
         };
-        if (kin) {
+        if (kin && !STREAM) {
             // keys formed by k_keys (same arithmetic as the projection below): copy and count
             const float4* src = reinterpret_cast<const float4*>(kin + (size_t)blockIdx.x * G * npad);
             for (int e = tid; e < G * npad / 4; e += NTK) {
@@ -606,9 +675,9 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                     xv[4 * c + 3] = t4.w;
                 }
                 const float ka = key_halves<D4>(ua, xv), kb = key_halves<D4>(ub, xv);
-                keys[(size_t)(2 * pair) * npad + i] = ka;
+                if (!STREAM) keys[(size_t)(2 * pair) * npad + i] = ka;
                 atomicAdd(&hist[(2 * pair) * NB + bucket_fma(ka, sca, ofa)], 1u);
-                keys[(size_t)(2 * pair + 1) * npad + i] = kb;
+                if (!STREAM) keys[(size_t)(2 * pair + 1) * npad + i] = kb;
                 atomicAdd(&hist[(2 * pair + 1) * NB + bucket_fma(kb, scb, ofb)], 1u);
             }
         } else if (DP4 > 0) {
@@ -678,14 +747,14 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     }
     __syncthreads();
 
-    select_dirs<G>(C, keys, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err);
+    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err);
 }
 
 }  // namespace
 
-size_t pdap_smem_bytes(int n, int group, int ldx)
+size_t pdap_smem_bytes(int n, int group, int ldx, bool stream)
 {
-    const size_t npad = ((size_t)n + 3) & ~(size_t)3;
+    const size_t npad = stream ? 0 : ((size_t)n + 3) & ~(size_t)3;
     return sizeof(float) * ((size_t)group * npad + (size_t)group * ldx) + sizeof(unsigned) * (size_t)group * NB +
            sizeof(float) * (size_t)group * 2 * CAP;
 }
@@ -798,30 +867,31 @@ __global__ void __launch_bounds__(256) k_keys(const TaskDev* __restrict__ tasks,
     }
 }
 
-template <int G, int DP4>
+template <int G, int DP4, bool STREAM>
 static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
                             const float* U, const float* z32, ResDev* res, int* err, const float* kin, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_pdap2<G, DP4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_pdap2<G, DP4, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<G, DP4><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err, kin);
+    k_pdap2<G, DP4, STREAM><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err, kin);
     return cudaGetLastError();
 }
 
-template <int G>
+template <int G, bool STREAM>
 static cudaError_t launch_g(int dp4, const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots,
                             const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, const float* kin,
                             cudaStream_t st)
 {
     switch (dp4) {
-    case 4: return launch_t<G, 4>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 8: return launch_t<G, 8>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 12: return launch_t<G, 12>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 16: return launch_t<G, 16>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    default: return launch_t<G, 0>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 4: return launch_t<G, 4, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 8: return launch_t<G, 8, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 12: return launch_t<G, 12, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 16: return launch_t<G, 16, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    default: return launch_t<G, 0, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
     }
 }
 
@@ -831,18 +901,44 @@ int pdap_dp4_class(int d)
     return dp4 <= 16 ? dp4 : 0;
 }
 
-cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
+cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
                         const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
                         const float* kin)
 {
     if (ntasks <= 0) return cudaSuccess;
     if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
+    const int dp4 = variant & ~PDAP_STREAM;
+    if (variant & PDAP_STREAM) {
+        if (group != PDAP_STREAM_GROUP || kin) return cudaErrorInvalidValue;
+        return launch_g<PDAP_STREAM_GROUP, true>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, nullptr, st);
+    }
     switch (group) {
-    case 1: return launch_g<1>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 2: return launch_g<2>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 4: return launch_g<4>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 1: return launch_g<1, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 2: return launch_g<2, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 4: return launch_g<4, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+PdapShape pdap_shape(int n, int ldx, int m, int d, int group)
+{
+    PdapShape s{};
+    const int dp4 = pdap_dp4_class(d);
+    int G = group;
+    if (G && (G > m || pdap_smem_bytes(n, G, ldx) > pdap_smem_limit())) G = 0;
+    if (!G) G = pdap_max_group(n, ldx, m, d, dp4 == 0);
+    if (G) {
+        s.group = G;
+        s.variant = dp4;
+        s.smem = pdap_smem_bytes(n, G, ldx);
+        s.keys_gemm = dp4 == 0;
+    } else {
+        s.group = PDAP_STREAM_GROUP;
+        s.variant = dp4 | PDAP_STREAM;
+        s.smem = pdap_smem_bytes(n, PDAP_STREAM_GROUP, ldx, true);
+        s.keys_gemm = false;
+    }
+    return s;
 }
 
 size_t pdap_keys_bytes(int n, int group, int ntasks)

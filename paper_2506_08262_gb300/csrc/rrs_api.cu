@@ -141,7 +141,7 @@ struct Plan {
     std::vector<TaskDev> gen_tasks, hd_tasks;
     std::vector<std::vector<TaskDev>> pd_tasks;       // one list per (shared-memory class, group, d class)
     std::vector<size_t> pd_smem;                      // bytes of each list's class
-    std::vector<int> pd_group, pd_dp4;
+    std::vector<int> pd_group, pd_variant;
     std::vector<int> pd_keys_ds;                      // d > 16: dataset whose keys k_keys forms first (-1: none)
     std::vector<int> pd_keys_chunk;                   // tasks per keys launch (bounded by the keys scratch)
     std::vector<int32_t> argmin_list;
@@ -235,8 +235,8 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
     // shared-memory classes for the selection kernel
     const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
     std::map<std::tuple<size_t, int, int, int>, int> pd_index;
-    auto pd_list = [&](size_t smem, int group, int dp4, int keys_ds) {
-        auto key = std::make_tuple(smem, group, dp4, keys_ds);
+    auto pd_list = [&](size_t smem, int group, int variant, int keys_ds) {
+        auto key = std::make_tuple(smem, group, variant, keys_ds);
         auto it = pd_index.find(key);
         if (it != pd_index.end()) return it->second;
         const int idx = (int)P.pd_tasks.size();
@@ -244,7 +244,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
         P.pd_tasks.emplace_back();
         P.pd_smem.push_back(smem);
         P.pd_group.push_back(group);
-        P.pd_dp4.push_back(dp4);
+        P.pd_variant.push_back(variant);
         P.pd_keys_ds.push_back(keys_ds);
         P.pd_keys_chunk.push_back(0);
         return idx;
@@ -264,23 +264,20 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
             return fail(RRS_ERR_UNSUPPORTED, "FP32 halfspace kernel stages 128 rows of d floats; d=%d too large", D.d);
         if (R.kind != RRS_HALFSPACE) {
             if (D.n > 0x7FFFFFFF) return fail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
-            G = P.force_group;
-            if (!G && P.tune) {
+            int want = P.force_group;
+            if (!want && P.tune) {
                 auto it = P.tune->find(std::make_tuple(D.n, D.ldx, m));
-                if (it != P.tune->end()) G = it->second;
+                if (it != P.tune->end()) want = it->second;
             }
-            if (G && (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())) G = 0;
-            if (!G) G = pdap_max_group((int)D.n, D.ldx, m, D.d, pdap_dp4_class(D.d) == 0);
-            if (G == 0)
-                return fail(RRS_ERR_UNSUPPORTED,
-                            "projection depth needs n*4 bytes of shared memory per direction; n=%lld is too large",
-                            (long long)D.n);
-            const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
-            // d > 16: keys come from a tiled GEMM (one list per dataset, since a GEMM launch reads one X)
-            const int keys_ds = pdap_dp4_class(D.d) == 0 ? dsidx[R.dset] : -1;
+            // resident keys when they fit shared memory, else keys recomputed at every pass
+            const PdapShape sh = pdap_shape((int)D.n, D.ldx, m, D.d, want);
+            G = sh.group;
+            // d > 16 with resident keys: keys come from a tiled GEMM (one list per dataset, since a GEMM
+            // launch reads one X)
+            const int keys_ds = sh.keys_gemm ? dsidx[R.dset] : -1;
             for (size_t c : classes)
-                if (need <= c) {
-                    cls = pd_list(c, G, pdap_dp4_class(D.d), keys_ds);
+                if (sh.smem <= c) {
+                    cls = pd_list(c, G, sh.variant, keys_ds);
                     break;
                 }
             if (cls < 0) return fail(RRS_ERR_INTERNAL, "no shared-memory class for n=%lld", (long long)D.n);
@@ -456,7 +453,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
             if (P.n_pd[c][l] <= 0) continue;
             if (P.pd_keys_ds[c] < 0) {
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
-                CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_dp4[c], P.d_slots,
+                CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
                                      P.d_ds, P.U, P.z32, P.res, ctx->d_err, st));
                 ctx->launches++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
@@ -469,7 +466,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap_keys(P.d_pd[c] + t0, cnt, P.pd_group[c], P.d_slots, P.d_ds, P.ds[P.pd_keys_ds[c]],
                                           P.U, P.keys, st));
-                CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_dp4[c], P.d_slots,
+                CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
                                      P.d_ds, P.U, P.z32, P.res, ctx->d_err, st, P.keys));
                 ctx->launches += 2;
                 ctx->stage_launches[RRS_STAGE_PDAP] += 2;
@@ -964,7 +961,7 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
             for (size_t c = 0; c < P.pd_tasks.size(); ++c)
                 if (!P.pd_tasks[c].empty())
                     CUDA_TRY(launch_pdap(P.d_pd[c], (int)P.pd_tasks[c].size(), P.pd_smem[c], P.pd_group[c],
-                                         P.pd_dp4[c], P.d_slots, P.d_ds, P.U,
+                                         P.pd_variant[c], P.d_slots, P.d_ds, P.U,
                                          P.z32, P.res, ctx->d_err, st));
         }
         ctx->launches += 4;

@@ -102,8 +102,9 @@ cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, c
 cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const SlotDev* slots, const DsDev* ds,
                            const float* U, const double* yz, const double* z64, ResDev* res, int64_t* band_out,
                            int* err, cudaStream_t st);
-// group: directions per CTA (1, 2 or 4, from pdap_max_group); dp4: pdap_dp4_class(d), shared by every task
-cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int dp4, const SlotDev* slots,
+// group: directions per CTA (1, 2 or 4, from pdap_shape); variant: pdap_shape's kernel variant (the key
+// arithmetic class pdap_dp4_class(d), plus PDAP_STREAM), shared by every task
+cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
                         const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
                         const float* kin = nullptr);
 // Keys of ntasks selection tasks (all of one dataset) by a tiled FP32 GEMM into keys
@@ -134,9 +135,24 @@ cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, i
 cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* center, float* cov, float* rc_out,
                            cudaStream_t st);
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
-size_t pdap_smem_bytes(int n, int group, int ldx);
+size_t pdap_smem_bytes(int n, int group, int ldx, bool stream = false);
 size_t pdap_smem_limit();
-int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // preferred G (0 if none fits)
+int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // preferred resident G (0 if none fits)
+
+// Selection-kernel variant bit: the keys are not held in shared memory but recomputed from X at every
+// pass (n beyond what shared memory holds for one direction); such launches take PDAP_STREAM_GROUP
+// directions per CTA and never read k_keys output.
+constexpr int PDAP_STREAM = 0x100;
+constexpr int PDAP_STREAM_GROUP = 2;
+struct PdapShape {
+    int group;        // directions per CTA
+    int variant;      // pdap_dp4_class(d), plus PDAP_STREAM
+    size_t smem;      // dynamic shared memory per CTA
+    bool keys_gemm;   // keys formed first by k_keys (d > 16, resident keys)
+};
+// Launch shape for a dataset (n rows, d dims, row stride ldx) and m directions per query; group > 0 asks for
+// that many resident directions per CTA (taken when it fits), 0 picks by the shared-memory heuristic.
+PdapShape pdap_shape(int n, int ldx, int m, int d, int group = 0);
 
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,

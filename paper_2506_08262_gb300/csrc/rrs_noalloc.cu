@@ -193,13 +193,22 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     const int m = (n_dirs + n_refinements - 1) / n_refinements;
     if (kind == RRS_HALFSPACE && ldx > 440)
         return noalloc_fail(RRS_ERR_UNSUPPORTED, "d=%d too large for the FP32 halfspace kernel", d);
-    int G = 0;
+    int G = 0, pd_variant = 0;
     size_t pd_smem = 0;
     if (kind != RRS_HALFSPACE) {
         if (n > 0x7FFFFFFF) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n too large");
-        G = pdap_max_group((int)n, ldx, m, d);
-        if (G == 0) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n=%lld too large for the selection kernel", (long long)n);
-        pd_smem = pdap_smem_bytes((int)n, G, ldx);
+        // keys formed inside the selection kernel (no k_keys scratch here): resident when they fit
+        // shared memory, else recomputed at every pass
+        int Gr = pdap_max_group((int)n, ldx, m, d);
+        if (Gr) {
+            G = Gr;
+            pd_variant = pdap_dp4_class(d);
+            pd_smem = pdap_smem_bytes((int)n, G, ldx);
+        } else {
+            G = PDAP_STREAM_GROUP;
+            pd_variant = pdap_dp4_class(d) | PDAP_STREAM;
+            pd_smem = pdap_smem_bytes((int)n, G, ldx, true);
+        }
     }
     const int gen_per = (m + 127) / 128;
     const int hd_tasks = (m + 63) / 64;
@@ -273,7 +282,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
         if (kind == RRS_HALFSPACE)
             NA_TRY(launch_hd_simt(hd, nq * hd_per, ldx, slots, ds, U, yz, z64, res, nullptr, err + 1, st));
         else
-            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, G, pdap_dp4_class(d), slots, ds, U, z32, res, err + 1, st));
+            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, G, pd_variant, slots, ds, U, z32, res, err + 1, st));
         NA_TRY(launch_argmin(slots, arg, nq, U, res, cur, nxt, l, 0, st));
     }
     int flags = 0;

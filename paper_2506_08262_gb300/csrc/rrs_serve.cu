@@ -315,7 +315,7 @@ rrs_status rrs_server_submit(rrs_server* S, int64_t dataset_id, const void* Z, i
     if (m > S->max_m || it->second.d > S->max_d || n_queries > S->cap)
         return sfail(RRS_ERR_UNSUPPORTED, "request exceeds the server's slot shape (m=%d, d=%d, nq=%lld)", m,
                      it->second.d, (long long)n_queries);
-    if (kind != RRS_HALFSPACE && pdap_max_group((int)it->second.n, it->second.ldx, m, it->second.d) == 0)
+    if (kind != RRS_HALFSPACE && it->second.n > 0x7FFFFFFF)
         return sfail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
     Request* R = new Request;
     R->id = S->next_id++;
@@ -347,23 +347,23 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
         std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
-        // selection lists per (shared-memory class, G, d class, dataset row for keys by k_keys or -1)
+        // selection lists per (shared-memory class, G, kernel variant, dataset row for keys by k_keys or -1)
         std::map<std::tuple<size_t, int, int, int>, std::vector<TaskDev>> pd;
         std::vector<int32_t> arg;
         const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
         for (Request* R : S->active) {
             const DsDev& D = S->ds_host[S->ds_index[R->dataset]];
-            int G = 0;
+            PdapShape sh{};
             size_t cls = 0;
             if (R->kind != RRS_HALFSPACE) {
-                G = pdap_max_group((int)D.n, D.ldx, R->m, D.d, pdap_dp4_class(D.d) == 0);
-                const size_t need = pdap_smem_bytes((int)D.n, G, D.ldx);
+                sh = pdap_shape((int)D.n, D.ldx, R->m, D.d);
                 for (size_t c : classes)
-                    if (need <= c) {
+                    if (sh.smem <= c) {
                         cls = c;
                         break;
                     }
             }
+            const int G = sh.group;
             const int hper = (R->m + ((R->m + 63) / 64) - 1) / ((R->m + 63) / 64);
             const int row = S->ds_index[R->dataset];
             const bool use_tc = R->kind == RRS_HALFSPACE && S->precision == RRS_PREC_SPLIT_BF16X3 && D.kp > 0;
@@ -376,8 +376,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 } else if (R->kind == RRS_HALFSPACE) {
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
                 } else {
-                    const int keys_row = pdap_dp4_class(D.d) == 0 ? row : -1;
-                    auto& v = pd[std::make_tuple(cls, G, pdap_dp4_class(D.d), keys_row)];
+                    const int keys_row = sh.keys_gemm ? row : -1;
+                    auto& v = pd[std::make_tuple(cls, G, sh.variant, keys_row)];
                     for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), 0});
                 }
                 arg.push_back(slot);

@@ -75,6 +75,26 @@ def test_batched_equals_alone(ctx, use_graph):
         ctx.free(did)
 
 
+def test_batched_mixes_recomputed_and_resident_keys(ctx):
+    # a dataset whose keys exceed shared memory (recomputed at every pass) batched with resident-key ones:
+    # each request's results equal its rrs_depth call alone
+    problems = []
+    for i, (n, d, kind) in enumerate([(60_000, 6, 1), (2_000, 6, 1), (61_003, 20, 2), (900, 20, 2), (3_000, 5, 0)]):
+        X, Z = workloads.gaussian_cloud(200 + i, n, d, 3, dtype=np.float32)
+        problems.append(workloads.Problem(X, Z, kind, 60, 3, 0.8, 0))
+    reqs, outs, ids = make_requests(ctx, problems)
+    stream = torch.cuda.current_stream()
+    rrs.rrs_depth_batched(ctx.handle, reqs, use_graph=False, stream=stream)
+    rrs.rrs_check(ctx.handle, stream)
+    for i, P in enumerate(problems):
+        d, c, b, ch = alone(ctx, ids[i], P, P.r, P.seed + i, outs[i]["Z"])
+        np.testing.assert_array_equal(outs[i]["depth"].cpu().numpy(), d)
+        np.testing.assert_array_equal(outs[i]["best"].cpu().numpy(), b)
+        np.testing.assert_array_equal(outs[i]["choice"].cpu().numpy(), ch)
+    for did in ids:
+        ctx.free(did)
+
+
 def test_batched_against_oracle_sample(ctx):
     problems = workloads.c4(seed=43, n_datasets=6, n_lo=100, n_hi=2000, q_hi=6, scale=1.0)
     for P in problems:

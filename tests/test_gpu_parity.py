@@ -270,18 +270,26 @@ def test_errors_are_reported_not_raised_on_device(ctx):
 
 
 @pytest.mark.parametrize("kind", [P, AP])
-def test_projection_depth_at_the_largest_n(ctx, kind):
-    # one direction per CTA with its keys in shared memory: n = 55,000 is near the 227 KB limit;
-    # a little beyond it the call is refused (no partial result, the context keeps working)
-    X, Z = workloads.gaussian_cloud(77, 55_000, 4, 3, dtype=np.float32)
-    g = gpu_rrs(ctx, X, Z, kind, 30, 2, 0.7, 2)
-    assert_follow(g, X, Z, kind, 30, 2, 0.7, 2)
-    Xb, Zb = workloads.gaussian_cloud(78, 60_000, 4, 2, dtype=np.float32)
-    with pytest.raises(rrs.RRSError) as e:
-        gpu_rrs(ctx, Xb, Zb, kind, 30, 2, 0.7, 2)
-    assert e.value.status == rrs.RRS_ERR_UNSUPPORTED
-    g2 = gpu_rrs(ctx, X[:500], Z, kind, 30, 2, 0.7, 2)
-    assert np.all((g2["depth"] >= 0) & (g2["depth"] <= 1))
+def test_projection_depth_either_side_of_the_shared_memory_limit(ctx, kind):
+    # one direction's 55,000 FP32 keys still fit a CTA's 227 KB of shared memory; 56,000 do not, and
+    # there every selection pass recomputes the keys from X: both sides against the oracle
+    for seed_data, n in ((77, 55_000), (78, 56_000)):
+        X, Z = workloads.gaussian_cloud(seed_data, n, 4, 3, dtype=np.float32)
+        g = gpu_rrs(ctx, X, Z, kind, 30, 2, 0.7, 2)
+        assert_follow(g, X, Z, kind, 30, 2, 0.7, 2)
+    X, Z = workloads.gaussian_cloud(79, 500, 4, 3, dtype=np.float32)
+    g2 = gpu_rrs(ctx, X, Z, kind, 30, 2, 0.7, 2)   # a resident-key dataset right after: no state carried over
+    assert_follow(g2, X, Z, kind, 30, 2, 0.7, 2)
+
+
+@pytest.mark.parametrize("kind", [P, AP])
+@pytest.mark.parametrize("n,d", [(70_001, 10), (65_000, 20), (120_000, 3)])
+def test_projection_depth_with_recomputed_keys(ctx, kind, n, d):
+    # keys recomputed at every pass: odd n (ragged tail of the four-wide scans), d > 16 (one sequential
+    # FMA chain per key instead of two half chains), and twice the shared-memory limit
+    X, Z = workloads.gaussian_cloud(90 + d, n, d, 2, dtype=np.float32)
+    g = gpu_rrs(ctx, X, Z, kind, 24, 2, 0.7, 5)
+    assert_follow(g, X, Z, kind, 24, 2, 0.7, 5)
 
 
 def test_zero_queries_is_a_no_op(ctx):

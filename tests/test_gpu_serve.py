@@ -140,3 +140,18 @@ def test_tensor_core_server_same_alone_and_in_the_mix(setup):
     for (did, Z, kind, seed), got, ref32 in zip(reqs, mix, fp32):
         np.testing.assert_array_equal(got, alone_depth(ctx, did, Z, kind, seed, precision=TCP))
         np.testing.assert_array_equal(got, ref32)
+
+
+def test_served_keys_beyond_shared_memory(setup):
+    # a projection-depth request on a dataset too large for resident keys, served between small ones
+    ctx, ds = setup
+    X, Zb = workloads.gaussian_cloud(57, 57_000, 8, 4, dtype=np.float32)
+    big = ctx.register(torch.from_numpy(X).cuda())
+    try:
+        reqs = [(ds[0][0], np.ascontiguousarray(ds[0][1].Z[:3]), 1, 11), (big, np.ascontiguousarray(Zb), 1, 12),
+                (big, np.ascontiguousarray(Zb[:2]), 2, 13), (ds[1][0], np.ascontiguousarray(ds[1][1].Z[:3]), 2, 14)]
+        got = serve(ctx, [reqs[:2], reqs[2:]])
+        for (did, Z, kind, seed), g in zip(reqs, got):
+            np.testing.assert_array_equal(g, alone_depth(ctx, did, Z, kind, seed))
+    finally:
+        ctx.free(big)

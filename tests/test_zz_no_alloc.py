@@ -58,6 +58,16 @@ def test_noalloc_matches_rrs_depth_two_calls_in_a_row(kind):
             assert np.all(got_c == -1)
 
 
+@pytest.mark.parametrize("kind", [rrs.RRS_PROJECTION, rrs.RRS_ASYM_PROJECTION])
+def test_noalloc_keys_beyond_shared_memory(kind):
+    # n = 58,000: the selection kernel recomputes the keys at every pass on both entry points
+    X, Z = workloads.gaussian_cloud(60 + kind, 58_000, 6, 5, dtype=np.float32)
+    Xd, Zd = torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda()
+    ref_d, _ = regular(Xd, Zd, kind, 40, 2, 0.7, 3)
+    got_d, _ = noalloc(Xd, Zd, kind, 40, 2, 0.7, 3)
+    np.testing.assert_allclose(got_d, ref_d, rtol=1e-5, atol=0)
+
+
 def test_noalloc_fp64_halfspace_and_a_different_second_call():
     # FP64 data (the exact recheck reads the caller's array), then a smaller call after a larger one
     P = workloads.c1()
