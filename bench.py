@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid", "ranks"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
                          "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
                          "grid: the paper's projection-depth timing grid (its Tables 1 and 2)")
@@ -855,6 +855,100 @@ def run_grid(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's center-outward ranking correlations (Sec. 6): Table 4 (Gaussian, d = 5 ... 150) and Table 5
+# (d = 50, Student t with nu = 1, 2, 5, 10), 5,000 points of n = 100,000, k = 100,000 over r = 40, alpha = 0.9.
+# Rows: the density against D_P, against D_AP, against the Mahalanobis depth with the sample mean and MLE
+# covariance, and D_P against D_AP.  (The robust MCD-based Mahalanobis rows are not reproduced.)
+PAPER_RANK_D = (5, 10, 25, 50, 100, 150)
+PAPER_RANK_NU = (1, 2, 5, 10)
+PAPER_TABLE4 = {
+    "spearman": {"pdf_dp": (.9999, .9998, .9995, .9987, .9963, .9912), "pdf_dap": (.9987, .9969, .9903, .9812, .9549, .9140),
+                 "pdf_dml": (.9999, .9998, .9998, .9996, .9993, .9990), "dp_dap": (.9987, .9971, .9907, .9810, .9536, .9115)},
+    "kendall": {"pdf_dp": (.9929, .9891, .9821, .9687, .9483, .9216), "pdf_dap": (.9697, .9530, .9172, .8820, .8157, .7468),
+                "pdf_dml": (.9945, .9921, .9892, .9848, .9793, .9741), "dp_dap": (.9704, .9545, .9187, .8813, .8123, .7431)},
+}
+PAPER_TABLE5 = {
+    "spearman": {"pdf_dp": (.9999, .9998, .9995, .9991), "pdf_dap": (.9996, .9992, .9982, .9967),
+                 "pdf_dml": (.9936, .9978, .9999, .9999), "dp_dap": (.9995, .9990, .9978, .9960)},
+    "kendall": {"pdf_dp": (.9907, .9871, .9804, .9741), "pdf_dap": (.9836, .9771, .9638, .9514),
+                "pdf_dml": (.9332, .9608, .9936, .9934), "dp_dap": (.9817, .9742, .9597, .9461)},
+}
+
+
+def run_ranks(args):
+    """Center-outward ordering on the paper's ranking data: D_P and D_AP of points drawn from an n = 100,000
+    cloud (keys beyond shared memory, so every selection pass recomputes them), rank-correlated with the
+    true density and with the Mahalanobis depth (sample mean, MLE covariance).  Defaults are a bounded
+    sample of the paper's run: --nq points (200) and --grid-k directions (20,000), r = 40, alpha = 0.9."""
+    import torch
+    from scipy.stats import kendalltau, spearmanr
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    ctx = rrs.rrs_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    n, r, alpha = 100_000, 40, 0.9
+    npts = args.nq or 200
+    k = (args.grid_k or [20_000])[0]
+    configs = [(d, np.inf) for d in PAPER_RANK_D if not args.grid_d or d in args.grid_d]
+    if not args.grid_d or 50 in args.grid_d:
+        configs += [(50, float(nu)) for nu in PAPER_RANK_NU]
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows, total_ms, total_q = [], 0.0, 0
+    for ci, (d, nu) in enumerate(configs):
+        X, Z, S = workloads.ranking_cloud(600 + ci, n, d, nu, npts)
+        did = rrs.rrs_register_dataset(ctx, torch.from_numpy(X).to(dev), n, d, rrs.RRS_F32, True)
+        Zd = torch.from_numpy(Z).to(dev)
+        depth, ms = {}, {}
+        for kind in (workloads.PROJECTION, workloads.ASYM_PROJECTION):
+            dep = torch.empty(npts, dtype=torch.float64, device=dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rrs.rrs_depth(ctx, did, Zd, npts, rrs.RRS_F32, True, kind, k, r, alpha, 0, rrs.RRS_PREC_FP32_SIMT,
+                          dep, None, None, None, True, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms[kind] = a.elapsed_time(b)
+            depth[kind] = dep.cpu().numpy()
+        rrs.rrs_check(ctx, stream)
+        rrs.rrs_free(ctx, did)
+        # the density is a decreasing function of z' S^-1 z for both families (mean 0, scatter S)
+        Zf = Z.astype(np.float64)
+        pdf_score = -np.einsum("ij,ij->i", Zf, np.linalg.solve(S, Zf.T).T)
+        Xf = X.astype(np.float64)
+        mu = Xf.mean(axis=0)
+        cov = (Xf - mu).T @ (Xf - mu) / n
+        dz = Zf - mu
+        dml = 1.0 / (1.0 + np.einsum("ij,ij->i", dz, np.linalg.solve(cov, dz.T).T))
+        dp, dap = depth[workloads.PROJECTION], depth[workloads.ASYM_PROJECTION]
+        pairs = {"pdf_dp": (pdf_score, dp), "pdf_dap": (pdf_score, dap), "pdf_dml": (pdf_score, dml),
+                 "dp_dap": (dp, dap)}
+        if np.isfinite(nu):
+            paper = {t: {key: PAPER_TABLE5[t][key][PAPER_RANK_NU.index(int(nu))] for key in pairs} for t in PAPER_TABLE5}
+        else:
+            paper = {t: {key: PAPER_TABLE4[t][key][PAPER_RANK_D.index(d)] for key in pairs} for t in PAPER_TABLE4}
+        rows.append({"d": d, "family": "gaussian" if not np.isfinite(nu) else f"student_t_nu{int(nu)}",
+                     "spearman": {key: round(float(spearmanr(x, y)[0]), 4) for key, (x, y) in pairs.items()},
+                     "kendall": {key: round(float(kendalltau(x, y)[0]), 4) for key, (x, y) in pairs.items()},
+                     "paper": paper, "ms": {"projection": round(ms[workloads.PROJECTION], 1),
+                                            "asymmetric": round(ms[workloads.ASYM_PROJECTION], 1)}})
+        total_ms += ms[workloads.PROJECTION] + ms[workloads.ASYM_PROJECTION]
+        total_q += 2 * npts
+    clocks = sampler.stop()
+    rrs.rrs_destroy(ctx)
+    line = {"metric": "center-outward ranking correlation (paper's Sec. 6)", "value": total_q / (total_ms / 1000),
+            "unit": "query-depths/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ranking: n = 100,000 N(0, Toeplitz 2^-|i-j|) (d = 5..150) or multivariate t "
+                                   "(nu = 1, 2, 5, 10; d = 50), query points drawn from the cloud, D_P and D_AP "
+                                   "with keys recomputed per selection pass",
+                       "points": npts, "k": k, "r": r, "alpha": alpha,
+                       "paper_run": "5,000 points, k = 100,000 (this run: a bounded sample)"},
+            "rows": rows, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -867,6 +961,8 @@ def main():
         run_c5(args)
     elif args.workload == "grid":
         run_grid(args)
+    elif args.workload == "ranks":
+        run_ranks(args)
     else:
         run_ours(args)
 

@@ -106,9 +106,11 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id);
  *   with an exact FP64 sign test.
  *   Projection depths take the exact median / MAD / MAD_+ of the FP32
  *   projections; while n FP32 keys per direction fit in shared memory they
- *   are held there, beyond that (n above ~55,000) every selection pass
- *   recomputes them from X with the same arithmetic, so results do not depend
- *   on which form ran.  n is limited to 2^31 - 1 for projection depths.
+ *   are held there; beyond that (n above ~55,000) they are formed once per
+ *   round in device memory (up to 256 MB of scratch, taken in chunks) and
+ *   every selection pass reads them back, with the same arithmetic, so results
+ *   do not depend on which form ran.  n is limited to 2^31 - 1 for projection
+ *   depths.
  * Outputs (each n_queries long, or n_queries*r for round_choice_out):
  *   depth_out[q]   final depth D_min (double).                      required
  *   count_out[q]   halfspace: min(#<=, #>=) at D_min, else -1.        optional
@@ -180,8 +182,8 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
  * with the same (n, d, m) use it.  Without tuning a shared-memory heuristic
  * decides.  Results never depend on the choice.  *choice_out (optional)
  * receives it (0 for halfspace depth, which has nothing to tune, and 0 when
- * no choice keeps the keys in shared memory: the kernel then recomputes them
- * at every pass with a fixed shape).
+ * no choice keeps the keys in shared memory: they then live in device memory
+ * and the kernel runs with a fixed shape).
  * Synchronous.  Errors: INVALID_ARG, NOT_FOUND, CUDA.
  */
 rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,

@@ -4,8 +4,10 @@
 //
 // One CTA handles G <= 4 directions of one query with the G*n keys resident in
 // shared memory, or, when n is beyond what shared memory holds, G = 2
-// directions whose keys are recomputed from X (same arithmetic, so the same
-// values) at every pass over them.  The whole CTA projects (pass A: every
+// directions whose keys stay outside: formed once by a keys kernel and read
+// from global memory at every pass, or (allocation-free entry point)
+// recomputed from X at every pass; the arithmetic is the same throughout, so
+// are the values.  The whole CTA projects (pass A: every
 // point on the G directions, keys stored, each added to a 2048-bucket histogram over
 // u'c +- 5 sigma_u, bucket = monotone FP32 map of the key).  Then the CTA
 // splits into G groups of (CTA threads)/G, one per direction, each synchronising
@@ -521,11 +523,12 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
 }
 
 // Every live direction of the CTA: group g of cta_threads<G>() / G threads handles direction g alone,
-// on its resident keys or (STREAM) on keys recomputed from X.
+// on its keys in shared memory or (STREAM) on keys formed by launch_pdap_keys in global memory (kin), else
+// on keys recomputed from X.
 template <int G, int DP4, bool STREAM>
 __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const float* uS, unsigned* hist, float* buf,
                                             int n, int npad, bool ap, const DsDev& D, int GA, int64_t roff,
-                                            ResDev* __restrict__ res, int* err)
+                                            ResDev* __restrict__ res, int* err, const float* kin)
 {
     constexpr int GS = cta_threads<G>() / G;   // threads per direction group
     const int tid = threadIdx.x;
@@ -534,7 +537,10 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
     if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
     unsigned* H = hist + g * NB;
     float* B0 = buf + (size_t)(2 * g) * CAP;   // two gather runs; FB_CAP = 2 * CAP for the fallback
-    if (STREAM) {
+    if (STREAM && kin) {
+        const KeysResident y{kin + ((size_t)blockIdx.x * G + g) * npad};
+        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+    } else if (STREAM) {
         const KeysRecomputed<DP4> y{D.X32, uS + (size_t)g * D.ldx, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
         select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
     } else {
@@ -545,8 +551,9 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
 
 // G: directions per CTA (compile time); DP4: d rounded up to 4 when <= 16 (the
 // directions are then held in registers), 0 for any d; STREAM: no keys in shared
-// memory, every pass recomputes them from X.
-// kin: optional precomputed keys, G x npad per task in launch order (k_keys), read instead of projecting
+// memory, every pass reads them from kin or recomputes them from X.
+// kin: optional precomputed keys, G x npad per task in launch order (launch_pdap_keys), read instead of
+// projecting
 template <int G, int DP4, bool STREAM>
 __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
@@ -635,8 +642,8 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
             }
         };
-        if (kin && !STREAM) {
-            // keys formed by k_keys (same arithmetic as the projection below): copy and count
+        if (kin) {
+            // keys formed by k_keys (same arithmetic as the projection below): count (and copy unless STREAM)
             const float4* src = reinterpret_cast<const float4*>(kin + (size_t)blockIdx.x * G * npad);
             for (int e = tid; e < G * npad / 4; e += NTK) {
                 const int g = e / (npad / 4), i = 4 * (e - g * (npad / 4));
@@ -646,7 +653,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     if (i + h < n) {
-                        keys[(size_t)g * npad + i + h] = kv[h];
+                        if (!STREAM) keys[(size_t)g * npad + i + h] = kv[h];
                         atomicAdd(&hist[g * NB + bucket_fma(kv[h], sc[g], of[g])], 1u);
                     }
                 }
@@ -747,7 +754,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     }
     __syncthreads();
 
-    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err);
+    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err, kin);
 }
 
 }  // namespace
@@ -867,6 +874,50 @@ __global__ void __launch_bounds__(256) k_keys(const TaskDev* __restrict__ tasks,
     }
 }
 
+// Keys for d <= 16 (DP4 = d rounded up to 4) with the selection kernel's own two-half-chain arithmetic
+// (key_halves), same layout as k_keys: keys[(t * G + g) * npad + i].  CTA: 256 points x 16 directions,
+// one point row in registers per thread, the directions in shared memory, coalesced key writes.
+constexpr int KH_P = 256, KH_D = 16;
+
+template <int DP4>
+__global__ void __launch_bounds__(KH_P) k_keys_halves(const TaskDev* __restrict__ tasks, int ntasks, int G,
+                                                      const SlotDev* __restrict__ slots,
+                                                      const DsDev* __restrict__ dsets, const float* __restrict__ U,
+                                                      float* __restrict__ keys, int npad)
+{
+    __shared__ __align__(16) float Us[KH_D][DP4];
+    __shared__ int live[KH_D];
+    const DsDev D = dsets[slots[tasks[0].slot].ds];
+    const int n = (int)D.n, ldx = D.ldx;
+    const int r0 = blockIdx.y * KH_D;
+    for (int e = threadIdx.x; e < KH_D * DP4; e += KH_P) {
+        const int rr = e / DP4, l = e - rr * DP4, r = r0 + rr, t = r / G, g = r - t * G;
+        float v = 0.0f;
+        if (t < ntasks && g < tasks[t].nj) v = U[slots[tasks[t].slot].uoff + (int64_t)(tasks[t].j0 + g) * ldx + l];
+        Us[rr][l] = v;
+    }
+    if (threadIdx.x < KH_D) {
+        const int r = r0 + threadIdx.x, t = r / G, g = r - t * G;
+        live[threadIdx.x] = t < ntasks && g < tasks[t].nj;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * KH_P + threadIdx.x;
+    if (i >= n) return;
+    const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+    float xv[DP4];
+#pragma unroll
+    for (int c = 0; c < DP4 / 4; ++c) {
+        const float4 t4 = xr[c];
+        xv[4 * c] = t4.x;
+        xv[4 * c + 1] = t4.y;
+        xv[4 * c + 2] = t4.z;
+        xv[4 * c + 3] = t4.w;
+    }
+#pragma unroll 4
+    for (int rr = 0; rr < KH_D; ++rr)
+        if (live[rr]) keys[(size_t)(r0 + rr) * npad + i] = key_halves<DP4>(Us[rr], xv);
+}
+
 template <int G, int DP4, bool STREAM>
 static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
                             const float* U, const float* z32, ResDev* res, int* err, const float* kin, cudaStream_t st)
@@ -909,8 +960,8 @@ cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group
     if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
     const int dp4 = variant & ~PDAP_STREAM;
     if (variant & PDAP_STREAM) {
-        if (group != PDAP_STREAM_GROUP || kin) return cudaErrorInvalidValue;
-        return launch_g<PDAP_STREAM_GROUP, true>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, nullptr, st);
+        if (group != PDAP_STREAM_GROUP) return cudaErrorInvalidValue;
+        return launch_g<PDAP_STREAM_GROUP, true>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
     }
     switch (group) {
     case 1: return launch_g<1, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
@@ -936,7 +987,9 @@ PdapShape pdap_shape(int n, int ldx, int m, int d, int group)
         s.group = PDAP_STREAM_GROUP;
         s.variant = dp4 | PDAP_STREAM;
         s.smem = pdap_smem_bytes(n, PDAP_STREAM_GROUP, ldx, true);
-        s.keys_gemm = false;
+        // the selection passes read keys formed once (k_keys, or k_keys_halves for d <= 16) instead of
+        // re-forming the dot products from X at every pass
+        s.keys_gemm = true;
     }
     return s;
 }
@@ -952,6 +1005,17 @@ cudaError_t launch_pdap_keys(const TaskDev* tasks, int ntasks, int group, const 
     if (ntasks <= 0) return cudaSuccess;
     if (ds_host.n < 1 || ds_host.n > 0x7FFFFFFF) return cudaErrorInvalidValue;
     const int npad = (int)((ds_host.n + 3) & ~3LL);
+    const int dp4 = pdap_dp4_class(ds_host.d);
+    if (dp4 > 0) {
+        const dim3 grid((unsigned)((ds_host.n + KH_P - 1) / KH_P), (unsigned)((ntasks * group + KH_D - 1) / KH_D));
+        switch (dp4) {
+        case 4: k_keys_halves<4><<<grid, KH_P, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad); break;
+        case 8: k_keys_halves<8><<<grid, KH_P, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad); break;
+        case 12: k_keys_halves<12><<<grid, KH_P, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad); break;
+        default: k_keys_halves<16><<<grid, KH_P, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad); break;
+        }
+        return cudaGetLastError();
+    }
     const dim3 grid((unsigned)((ds_host.n + KT_P - 1) / KT_P), (unsigned)((ntasks * group + KT_D - 1) / KT_D));
     k_keys<<<grid, 256, 0, st>>>(tasks, ntasks, group, slots, ds, U, keys, npad);
     return cudaGetLastError();

@@ -269,11 +269,11 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
                 auto it = P.tune->find(std::make_tuple(D.n, D.ldx, m));
                 if (it != P.tune->end()) want = it->second;
             }
-            // resident keys when they fit shared memory, else keys recomputed at every pass
+            // resident keys when they fit shared memory, else keys formed once and read at every pass
             const PdapShape sh = pdap_shape((int)D.n, D.ldx, m, D.d, want);
             G = sh.group;
-            // d > 16 with resident keys: keys come from a tiled GEMM (one list per dataset, since a GEMM
-            // launch reads one X)
+            // keys formed first by a keys kernel (d > 16, or keys outside shared memory): one list per
+            // dataset, since a keys launch reads one X
             const int keys_ds = sh.keys_gemm ? dsidx[R.dset] : -1;
             for (size_t c : classes)
                 if (sh.smem <= c) {

@@ -107,9 +107,10 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
                         const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
                         const float* kin = nullptr);
-// Keys of ntasks selection tasks (all of one dataset) by a tiled FP32 GEMM into keys
-// (pdap_keys_bytes), for launch_pdap(..., kin = keys) on the same task range; used for d > 16,
-// where forming the keys inside the selection kernel re-reads X for every G directions
+// Keys of ntasks selection tasks (all of one dataset) into keys (pdap_keys_bytes), for
+// launch_pdap(..., kin = keys) on the same task range, with the selection kernel's own key arithmetic:
+// a tiled FP32 GEMM for d > 16 (where forming the keys inside the selection kernel re-reads X for every
+// G directions), two half chains per key for d <= 16 (used when the keys do not fit shared memory)
 size_t pdap_keys_bytes(int n, int group, int ntasks);
 cudaError_t launch_pdap_keys(const TaskDev* tasks, int ntasks, int group, const SlotDev* slots, const DsDev* ds,
                              const DsDev& ds_host, const float* U, float* keys, cudaStream_t st);
@@ -139,16 +140,16 @@ size_t pdap_smem_bytes(int n, int group, int ldx, bool stream = false);
 size_t pdap_smem_limit();
 int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // preferred resident G (0 if none fits)
 
-// Selection-kernel variant bit: the keys are not held in shared memory but recomputed from X at every
-// pass (n beyond what shared memory holds for one direction); such launches take PDAP_STREAM_GROUP
-// directions per CTA and never read k_keys output.
+// Selection-kernel variant bit: the keys are not held in shared memory (n beyond what shared memory holds
+// for one direction); every pass reads them from k_keys output in global memory when given (kin), else
+// recomputes them from X.  Such launches take PDAP_STREAM_GROUP directions per CTA.
 constexpr int PDAP_STREAM = 0x100;
 constexpr int PDAP_STREAM_GROUP = 2;
 struct PdapShape {
     int group;        // directions per CTA
     int variant;      // pdap_dp4_class(d), plus PDAP_STREAM
     size_t smem;      // dynamic shared memory per CTA
-    bool keys_gemm;   // keys formed first by k_keys (d > 16, resident keys)
+    bool keys_gemm;   // keys formed first by launch_pdap_keys
 };
 // Launch shape for a dataset (n rows, d dims, row stride ldx) and m directions per query; group > 0 asks for
 // that many resident directions per CTA (taken when it fits), 0 picks by the shared-memory heuristic.

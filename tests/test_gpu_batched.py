@@ -75,8 +75,8 @@ def test_batched_equals_alone(ctx, use_graph):
         ctx.free(did)
 
 
-def test_batched_mixes_recomputed_and_resident_keys(ctx):
-    # a dataset whose keys exceed shared memory (recomputed at every pass) batched with resident-key ones:
+def test_batched_mixes_outside_and_resident_keys(ctx):
+    # datasets whose keys exceed shared memory (kept in device memory) batched with resident-key ones:
     # each request's results equal its rrs_depth call alone
     problems = []
     for i, (n, d, kind) in enumerate([(60_000, 6, 1), (2_000, 6, 1), (61_003, 20, 2), (900, 20, 2), (3_000, 5, 0)]):

@@ -272,7 +272,7 @@ def test_errors_are_reported_not_raised_on_device(ctx):
 @pytest.mark.parametrize("kind", [P, AP])
 def test_projection_depth_either_side_of_the_shared_memory_limit(ctx, kind):
     # one direction's 55,000 FP32 keys still fit a CTA's 227 KB of shared memory; 56,000 do not, and
-    # there every selection pass recomputes the keys from X: both sides against the oracle
+    # there the keys live in device memory and every selection pass reads them: both sides against the oracle
     for seed_data, n in ((77, 55_000), (78, 56_000)):
         X, Z = workloads.gaussian_cloud(seed_data, n, 4, 3, dtype=np.float32)
         g = gpu_rrs(ctx, X, Z, kind, 30, 2, 0.7, 2)
@@ -284,9 +284,9 @@ def test_projection_depth_either_side_of_the_shared_memory_limit(ctx, kind):
 
 @pytest.mark.parametrize("kind", [P, AP])
 @pytest.mark.parametrize("n,d", [(70_001, 10), (65_000, 20), (120_000, 3)])
-def test_projection_depth_with_recomputed_keys(ctx, kind, n, d):
-    # keys recomputed at every pass: odd n (ragged tail of the four-wide scans), d > 16 (one sequential
-    # FMA chain per key instead of two half chains), and twice the shared-memory limit
+def test_projection_depth_keys_outside_shared_memory(ctx, kind, n, d):
+    # keys outside shared memory, formed once by the keys kernels and read by every selection pass: odd n
+    # (ragged tail of the four-wide scans), d > 16 (tiled GEMM keys) and twice the shared-memory limit
     X, Z = workloads.gaussian_cloud(90 + d, n, d, 2, dtype=np.float32)
     g = gpu_rrs(ctx, X, Z, kind, 24, 2, 0.7, 5)
     assert_follow(g, X, Z, kind, 24, 2, 0.7, 5)

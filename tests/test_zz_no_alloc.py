@@ -59,9 +59,11 @@ def test_noalloc_matches_rrs_depth_two_calls_in_a_row(kind):
 
 
 @pytest.mark.parametrize("kind", [rrs.RRS_PROJECTION, rrs.RRS_ASYM_PROJECTION])
-def test_noalloc_keys_beyond_shared_memory(kind):
-    # n = 58,000: the selection kernel recomputes the keys at every pass on both entry points
-    X, Z = workloads.gaussian_cloud(60 + kind, 58_000, 6, 5, dtype=np.float32)
+@pytest.mark.parametrize("d", [6, 20])
+def test_noalloc_keys_beyond_shared_memory(kind, d):
+    # n = 58,000: keys outside shared memory; the allocation-free entry point recomputes them at every
+    # pass, the regular one forms them once (keys kernels, same arithmetic) and reads them at every pass
+    X, Z = workloads.gaussian_cloud(60 + kind, 58_000, d, 5, dtype=np.float32)
     Xd, Zd = torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda()
     ref_d, _ = regular(Xd, Zd, kind, 40, 2, 0.7, 3)
     got_d, _ = noalloc(Xd, Zd, kind, 40, 2, 0.7, 3)

@@ -183,6 +183,27 @@ def gaussian_cloud(seed: int, n: int, d: int, nq: int, dtype=np.float64, zscale:
     return np.ascontiguousarray(X, dtype=dtype), np.ascontiguousarray(Z, dtype=dtype)
 
 
+def toeplitz_scatter(d: int) -> np.ndarray:
+    """The paper's Toeplitz matrix sigma_ij = 2^{-|i-j|} (Sec. 5)."""
+    idx = np.arange(d)
+    return 2.0 ** (-np.abs(idx[:, None] - idx[None, :]))
+
+
+def ranking_cloud(seed: int, n: int, d: int, nu: float, npts: int, dtype=np.float32):
+    """The center-outward ranking data of Sec. 6: n points of N(0, S) (nu = inf) or of the multivariate
+    Student-t with nu degrees of freedom and scatter S (a N(0, S) draw divided by sqrt(w / nu), w ~ chi2_nu),
+    S = toeplitz_scatter(d), and npts of them chosen at random as query points.  Returns (X, Z, S)."""
+    rng = np.random.default_rng(seed)
+    S = toeplitz_scatter(d)
+    L = np.linalg.cholesky(S)
+    X = rng.standard_normal((n, d)) @ L.T
+    if np.isfinite(nu):
+        X = X / np.sqrt(rng.chisquare(nu, size=n) / nu)[:, None]
+    idx = rng.choice(n, size=npts, replace=False)
+    X = np.ascontiguousarray(X, dtype=dtype)
+    return X, np.ascontiguousarray(X[idx]), S
+
+
 def toeplitz_gaussian(seed: int, n: int, d: int, nq: int, dtype=np.float32):
     """N(0, Sigma) with sigma_ij = 2^{-|i-j|} (the paper's Sec. 5 generator)."""
     rng = np.random.default_rng(seed)
