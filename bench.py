@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid", "ranks"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
                          "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
-                         "grid: the paper's projection-depth timing grid (its Tables 1 and 2)")
+                         "grid: the paper's projection-depth timing grid (its Tables 1 and 2); "
+                         "ranks: its center-outward ranking correlations (Tables 4 and 5)")
     ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
     ap.add_argument("--sweep", action="store_true", help="c5: serve the stream at 1/8 .. 2x --rate and report each")
     ap.add_argument("--grid-d", type=int, nargs="*", default=None, help="grid: only these dimensions")
@@ -878,8 +879,9 @@ PAPER_TABLE5 = {
 def run_ranks(args):
     """Center-outward ordering on the paper's ranking data: D_P and D_AP of points drawn from an n = 100,000
     cloud (keys beyond shared memory, so every selection pass recomputes them), rank-correlated with the
-    true density and with the Mahalanobis depth (sample mean, MLE covariance).  Defaults are a bounded
-    sample of the paper's run: --nq points (200) and --grid-k directions (20,000), r = 40, alpha = 0.9."""
+    true density and with the Mahalanobis depth (sample mean, MLE covariance).  The paper's k = 100,000
+    directions over r = 40 rounds, alpha = 0.9, on a bounded sample of its 5,000 points: --nq (100);
+    --grid-k overrides k."""
     import torch
     from scipy.stats import kendalltau, spearmanr
     from __graft_entry__ import build
@@ -889,8 +891,8 @@ def run_ranks(args):
     ctx = rrs.rrs_create(0, 0)
     stream = torch.cuda.current_stream(dev)
     n, r, alpha = 100_000, 40, 0.9
-    npts = args.nq or 200
-    k = (args.grid_k or [20_000])[0]
+    npts = args.nq or 100
+    k = (args.grid_k or [100_000])[0]
     configs = [(d, np.inf) for d in PAPER_RANK_D if not args.grid_d or d in args.grid_d]
     if not args.grid_d or 50 in args.grid_d:
         configs += [(50, float(nu)) for nu in PAPER_RANK_NU]
@@ -944,7 +946,7 @@ def run_ranks(args):
                                    "(nu = 1, 2, 5, 10; d = 50), query points drawn from the cloud, D_P and D_AP "
                                    "with keys recomputed per selection pass",
                        "points": npts, "k": k, "r": r, "alpha": alpha,
-                       "paper_run": "5,000 points, k = 100,000 (this run: a bounded sample)"},
+                       "paper_run": "5,000 points, k = 100,000 (this run: a bounded sample of points)"},
             "rows": rows, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
