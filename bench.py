@@ -63,11 +63,12 @@ def parse():
                     help="headline: keep the shared-memory heuristic for the selection kernel's directions per CTA")
     ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid", "ranks"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid", "ranks", "convergence"], default="c2",
                     help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
                          "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
                          "grid: the paper's projection-depth timing grid (its Tables 1 and 2); "
-                         "ranks: its center-outward ranking correlations (Tables 4 and 5)")
+                         "ranks: its center-outward ranking correlations (Tables 4 and 5); "
+                         "convergence: its cap-shrinkage convergence study (Sec. 5.1)")
     ap.add_argument("--scale", type=float, default=1.0, help="c4/c5: shrink n and query counts (tests)")
     ap.add_argument("--sweep", action="store_true", help="c5: serve the stream at 1/8 .. 2x --rate and report each")
     ap.add_argument("--grid-d", type=int, nargs="*", default=None, help="grid: only these dimensions")
@@ -956,6 +957,76 @@ def run_ranks(args):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(args):
+    """The paper's cap-shrinkage convergence study (Sec. 5.1) for D_P: n = 50,000 normal points in d = 50
+    (Toeplitz covariance), --nq points (50) drawn from the cloud, a reference depth per point = the minimum
+    over three seeds of r = 100, alpha = 0.9 runs with --grid-k directions (1,000,000; the paper uses
+    3,000,000), then the mean squared error to it over alpha in {0.6, 0.7, 0.8, 0.9}, r in {25, 30, 35} and
+    k from 200 to 90,000.  All 108 grid cells run as requests of one rrs_depth_batched call."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    ctx = rrs.rrs_create(0, 0)
+    stream = torch.cuda.current_stream(dev)
+    n, d = 50_000, 50
+    npts = args.nq or 50
+    k_ref = (args.grid_k or [1_000_000])[0]
+    X, Z, _ = workloads.ranking_cloud(700, n, d, np.inf, npts)
+    did = rrs.rrs_register_dataset(ctx, torch.from_numpy(X).to(dev), n, d, rrs.RRS_F32, True)
+    Zd = torch.from_numpy(Z).to(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+
+    def batched(cells):
+        outs, reqs = [], []
+        for (k, r, alpha, seed) in cells:
+            o = torch.empty(npts, dtype=torch.float64, device=dev)
+            outs.append(o)
+            reqs.append(rrs.rrs_request(dataset_id=did, Z=Zd.data_ptr(), n_queries=npts, dtype=rrs.RRS_F32,
+                                        kind=rrs.RRS_PROJECTION, n_dirs=k, n_refinements=r, cap_shrink=alpha,
+                                        seed=seed, depth_out=o.data_ptr(), precision=rrs.RRS_PREC_FP32_SIMT))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rrs.rrs_depth_batched(ctx, reqs, use_graph=False, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rrs.rrs_check(ctx, stream)
+        return [o.cpu().numpy() for o in outs], a.elapsed_time(b), sum(k for k, _, _, _ in cells) * npts * n
+
+    ref_runs, ref_ms, ref_pd = batched([(k_ref, 100, 0.9, s) for s in (101, 102, 103)])
+    ref = np.minimum.reduce(ref_runs)
+    alphas, rs, ks = (0.6, 0.7, 0.8, 0.9), (25, 30, 35), (200, 500, 1_000, 2_000, 5_000, 10_000, 20_000, 50_000, 90_000)
+    cells = [(k, r, a, 7) for a in alphas for r in rs for k in ks]
+    got, grid_ms, grid_pd = batched(cells)
+    clocks = sampler.stop()
+    rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    mse = {}
+    below = 0
+    for (k, r, a, _), g in zip(cells, got):
+        mse.setdefault(f"alpha={a}", {}).setdefault(f"r={r}", {})[k] = float(np.mean((g - ref) ** 2))
+        below += int(np.sum(g < ref))
+    # the paper's reading of its figure: larger alpha converges faster; summarised here per alpha as the
+    # mean over r of the MSE at each k
+    by_alpha = {a: [float(np.mean([mse[a][rk][k] for rk in mse[a]])) for k in ks] for a in mse}
+    line = {"metric": "convergence of D_P to the reference depth (paper's Sec. 5.1)", "value": float(by_alpha["alpha=0.9"][-1]),
+            "unit": "mean squared error at alpha = 0.9, k = 90,000 (mean over r)", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "convergence: n = 50,000 N(0, Toeplitz 2^-|i-j|), d = 50, points drawn from "
+                                   "the cloud, D_P; grid alpha x r x k in one batched call",
+                       "points": npts, "reference": {"k": k_ref, "r": 100, "alpha": 0.9, "seeds": 3,
+                                                     "paper": "k = 3,000,000"},
+                       "grid": {"alpha": alphas, "r": rs, "k": ks}},
+            "mse_by_alpha_mean_over_r": {"k": ks, **by_alpha}, "mse": mse,
+            "grid_depths_below_reference": below,
+            "timing": {"reference_s": ref_ms / 1000, "reference_pd_per_s": ref_pd / (ref_ms / 1000),
+                       "grid_s": grid_ms / 1000, "grid_pd_per_s": grid_pd / (grid_ms / 1000)},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -970,6 +1041,8 @@ def main():
         run_grid(args)
     elif args.workload == "ranks":
         run_ranks(args)
+    elif args.workload == "convergence":
+        run_convergence(args)
     else:
         run_ours(args)
 
