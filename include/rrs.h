@@ -41,7 +41,7 @@ typedef int32_t rrs_status;
 #define RRS_ERR_CUDA (-4)        /* a CUDA runtime call failed (see rrs_last_error) */
 #define RRS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
 #define RRS_ERR_INTERNAL (-6)    /* an internal invariant failed */
-#define RRS_ERR_UNSUPPORTED (-7) /* valid request this build cannot serve (e.g. d too large) */
+#define RRS_ERR_UNSUPPORTED (-7) /* valid request the library cannot serve (e.g. d too large) */
 
 /* Element types of X and Z. */
 #define RRS_F32 0
