@@ -292,6 +292,29 @@ def test_projection_depth_keys_outside_shared_memory(ctx, kind, n, d):
     assert_follow(g, X, Z, kind, 24, 2, 0.7, 5)
 
 
+@pytest.mark.parametrize("kind", [P, AP])
+@pytest.mark.parametrize("n", [20_000, 60_000])
+def test_projection_depth_heavy_tails(ctx, kind, n):
+    # multivariate t with one degree of freedom: bucket ranges from the covariance are far too wide, so
+    # selections go through the iterated-bucket fallback, with keys in shared memory (n = 20,000) and in
+    # device memory (n = 60,000)
+    X, Z, _ = workloads.ranking_cloud(300 + n % 7, n, 5, 1.0, 3)
+    g = gpu_rrs(ctx, X, Z, kind, 24, 2, 0.7, 8)
+    assert_follow(g, X, Z, kind, 24, 2, 0.7, 8)
+
+
+@pytest.mark.parametrize("kind", [P, AP])
+@pytest.mark.parametrize("n", [20_000, 60_000])
+def test_projection_depth_lattice_ties(ctx, kind, n):
+    # 343 distinct rows repeated ~n/343 times: long runs of equal keys around the median and the MAD,
+    # beyond the gather buffer, resolved exactly
+    rng = np.random.default_rng(n)
+    X = rng.integers(-3, 4, size=(n, 3)).astype(np.float32)
+    Z = np.array([[0, 0, 0], [1, -1, 2], [3, 3, 3]], np.float32)
+    g = gpu_rrs(ctx, X, Z, kind, 24, 2, 0.7, 9)
+    assert_follow(g, X, Z, kind, 24, 2, 0.7, 9)
+
+
 def test_zero_queries_is_a_no_op(ctx):
     X = np.ones((4, 2), np.float32)
     did = rrs.rrs_register_dataset(ctx.handle, X, 4, 2, rrs.RRS_F32, False)
