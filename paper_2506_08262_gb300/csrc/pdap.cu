@@ -296,8 +296,9 @@ __device__ __forceinline__ float key_halves(const float* u, const float* x)
     return __fadd_rn(p0, p1);
 }
 
-// One direction's keys held in shared memory.
-struct KeysResident {
+// One direction's keys held in an array: shared memory (resident keys) or device memory (keys formed
+// by launch_pdap_keys when they do not fit shared memory).
+struct KeysArray {
     const float* y;
     __device__ __forceinline__ float get(int i) const { return y[i]; }
     __device__ __forceinline__ float4 get4(int i) const { return *reinterpret_cast<const float4*>(y + i); }
@@ -538,13 +539,13 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
     unsigned* H = hist + g * NB;
     float* B0 = buf + (size_t)(2 * g) * CAP;   // two gather runs; FB_CAP = 2 * CAP for the fallback
     if (STREAM && kin) {
-        const KeysResident y{kin + ((size_t)blockIdx.x * G + g) * npad};
+        const KeysArray y{kin + ((size_t)blockIdx.x * G + g) * npad};
         select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
     } else if (STREAM) {
         const KeysRecomputed<DP4> y{D.X32, uS + (size_t)g * D.ldx, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
         select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
     } else {
-        const KeysResident y{keys + (size_t)g * npad};
+        const KeysArray y{keys + (size_t)g * npad};
         select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
     }
 }
