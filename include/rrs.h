@@ -109,7 +109,7 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id);
  *   are held there; beyond that (n above ~55,000) they are formed once per
  *   round in device memory (up to 256 MB of scratch, taken in chunks) and
  *   every selection pass reads them back, with the same arithmetic, so results
- *   do not depend on which form ran.  n is limited to 2^31 - 1 for projection
+ *   do not depend on which form ran.  n is limited to 2^31 - 64 for projection
  *   depths.
  * Outputs (each n_queries long, or n_queries*r for round_choice_out):
  *   depth_out[q]   final depth D_min (double).                      required

@@ -1004,7 +1004,7 @@ cudaError_t launch_pdap_keys(const TaskDev* tasks, int ntasks, int group, const 
                              const DsDev& ds_host, const float* U, float* keys, cudaStream_t st)
 {
     if (ntasks <= 0) return cudaSuccess;
-    if (ds_host.n < 1 || ds_host.n > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    if (ds_host.n < 1 || ds_host.n > PDAP_MAX_N) return cudaErrorInvalidValue;
     const int npad = (int)((ds_host.n + 3) & ~3LL);
     const int dp4 = pdap_dp4_class(ds_host.d);
     if (dp4 > 0) {

@@ -263,7 +263,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
         if (R.kind == RRS_HALFSPACE && !tc && D.ldx > 440)
             return fail(RRS_ERR_UNSUPPORTED, "FP32 halfspace kernel stages 128 rows of d floats; d=%d too large", D.d);
         if (R.kind != RRS_HALFSPACE) {
-            if (D.n > 0x7FFFFFFF) return fail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
+            if (D.n > PDAP_MAX_N) return fail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
             int want = P.force_group;
             if (!want && P.tune) {
                 auto it = P.tune->find(std::make_tuple(D.n, D.ldx, m));

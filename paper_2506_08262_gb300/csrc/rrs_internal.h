@@ -144,6 +144,8 @@ int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // pre
 // for one direction); every pass reads them from k_keys output in global memory when given (kin), else
 // recomputes them from X.  Such launches take PDAP_STREAM_GROUP directions per CTA.
 constexpr int PDAP_STREAM = 0x100;
+// Largest n the selection kernels take: point indices and the padded key count (n rounded up to 4) are int.
+constexpr int64_t PDAP_MAX_N = 0x7FFFFFC0;
 constexpr int PDAP_STREAM_GROUP = 2;
 struct PdapShape {
     int group;        // directions per CTA

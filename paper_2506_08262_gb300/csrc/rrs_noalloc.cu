@@ -196,7 +196,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     int G = 0, pd_variant = 0;
     size_t pd_smem = 0;
     if (kind != RRS_HALFSPACE) {
-        if (n > 0x7FFFFFFF) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n too large");
+        if (n > PDAP_MAX_N) return noalloc_fail(RRS_ERR_UNSUPPORTED, "n too large");
         // keys formed inside the selection kernel (no k_keys scratch here): resident when they fit
         // shared memory, else recomputed at every pass
         int Gr = pdap_max_group((int)n, ldx, m, d);

@@ -315,7 +315,7 @@ rrs_status rrs_server_submit(rrs_server* S, int64_t dataset_id, const void* Z, i
     if (m > S->max_m || it->second.d > S->max_d || n_queries > S->cap)
         return sfail(RRS_ERR_UNSUPPORTED, "request exceeds the server's slot shape (m=%d, d=%d, nq=%lld)", m,
                      it->second.d, (long long)n_queries);
-    if (kind != RRS_HALFSPACE && it->second.n > 0x7FFFFFFF)
+    if (kind != RRS_HALFSPACE && it->second.n > PDAP_MAX_N)
         return sfail(RRS_ERR_UNSUPPORTED, "n too large for the selection kernel");
     Request* R = new Request;
     R->id = S->next_id++;
