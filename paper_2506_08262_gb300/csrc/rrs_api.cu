@@ -140,7 +140,7 @@ struct Plan {
     std::vector<SlotDev> slots;
     std::vector<TaskDev> gen_tasks, hd_tasks;
     std::vector<std::vector<TaskDev>> pd_tasks;       // one list per (shared-memory class, group, d class)
-    std::vector<size_t> pd_smem;                      // bytes of each list's class
+    std::vector<size_t> pd_smem;                      // dynamic shared memory of each list: its largest need
     std::vector<int> pd_group, pd_variant;
     std::vector<int> pd_keys_ds;                      // d > 16: dataset whose keys k_keys forms first (-1: none)
     std::vector<int> pd_keys_chunk;                   // tasks per keys launch (bounded by the keys scratch)
@@ -232,17 +232,21 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
             P.ds.push_back(dd);
         }
     }
-    // shared-memory classes for the selection kernel
+    // shared-memory classes group the selection launches; each launch requests the largest need of its
+    // class, not the class bound, so small needs keep more of the SM's memory as L1
     const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
     std::map<std::tuple<size_t, int, int, int>, int> pd_index;
-    auto pd_list = [&](size_t smem, int group, int variant, int keys_ds) {
-        auto key = std::make_tuple(smem, group, variant, keys_ds);
+    auto pd_list = [&](size_t cls_bytes, size_t need, int group, int variant, int keys_ds) {
+        auto key = std::make_tuple(cls_bytes, group, variant, keys_ds);
         auto it = pd_index.find(key);
-        if (it != pd_index.end()) return it->second;
+        if (it != pd_index.end()) {
+            P.pd_smem[it->second] = std::max(P.pd_smem[it->second], need);
+            return it->second;
+        }
         const int idx = (int)P.pd_tasks.size();
         pd_index[key] = idx;
         P.pd_tasks.emplace_back();
-        P.pd_smem.push_back(smem);
+        P.pd_smem.push_back(need);
         P.pd_group.push_back(group);
         P.pd_variant.push_back(variant);
         P.pd_keys_ds.push_back(keys_ds);
@@ -277,7 +281,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
             const int keys_ds = sh.keys_gemm ? dsidx[R.dset] : -1;
             for (size_t c : classes)
                 if (sh.smem <= c) {
-                    cls = pd_list(c, G, sh.variant, keys_ds);
+                    cls = pd_list(c, sh.smem, G, sh.variant, keys_ds);
                     break;
                 }
             if (cls < 0) return fail(RRS_ERR_INTERNAL, "no shared-memory class for n=%lld", (long long)D.n);

@@ -347,8 +347,10 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
         std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
-        // selection lists per (shared-memory class, G, kernel variant, dataset row for keys by k_keys or -1)
+        // selection lists per (shared-memory class, G, kernel variant, dataset row for keys by k_keys or -1);
+        // each launch requests the largest shared-memory need of its list
         std::map<std::tuple<size_t, int, int, int>, std::vector<TaskDev>> pd;
+        std::map<std::tuple<size_t, int, int, int>, size_t> pd_need;
         std::vector<int32_t> arg;
         const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
         for (Request* R : S->active) {
@@ -377,7 +379,10 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
                 } else {
                     const int keys_row = sh.keys_gemm ? row : -1;
-                    auto& v = pd[std::make_tuple(cls, G, sh.variant, keys_row)];
+                    const auto key = std::make_tuple(cls, G, sh.variant, keys_row);
+                    auto& v = pd[key];
+                    size_t& need = pd_need[key];
+                    need = std::max(need, sh.smem);
                     for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), 0});
                 }
                 arg.push_back(slot);
@@ -419,7 +424,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             const TaskDev* tl = (const TaskDev*)(T + po.first);
             const int cnt_all = (int)pd[key].size(), G = std::get<1>(key), krow = std::get<3>(key);
             if (krow < 0) {
-                S_TRY(launch_pdap(tl, cnt_all, std::get<0>(key), G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
+                S_TRY(launch_pdap(tl, cnt_all, pd_need[key], G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
                                   S->d_z32, S->d_res, S->ctx->d_err, S->st));
                 continue;
             }
@@ -439,7 +444,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 const int cnt = std::min(chunk, cnt_all - t0);
                 S_TRY(launch_pdap_keys(tl + t0, cnt, G, S->d_slots, S->d_ds, S->ds_host[krow], S->d_U, S->d_keys,
                                        S->st));
-                S_TRY(launch_pdap(tl + t0, cnt, std::get<0>(key), G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
+                S_TRY(launch_pdap(tl + t0, cnt, pd_need[key], G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
                                   S->d_z32, S->d_res, S->ctx->d_err, S->st, S->d_keys));
                 extra += 2;
             }
