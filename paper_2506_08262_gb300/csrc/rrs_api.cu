@@ -434,7 +434,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
         float* nxt = P.poles + ((l + 1) & 1) * T;
         if (P.n_gen[l] > 0) {
             StageTimer t(ctx, RRS_STAGE_GEN, st, capturing);
-            CUDA_TRY(launch_gen(P.d_gen, P.n_gen[l], P.d_slots, cur, P.z64, P.U, P.yz, l, st));
+            CUDA_TRY(launch_gen(P.d_gen, P.n_gen[l], P.d_slots, cur, P.z64, P.U, P.yz, l, P.max_ldx, st));
             ctx->launches++;
             ctx->stage_launches[RRS_STAGE_GEN]++;
         }

@@ -97,8 +97,9 @@ void set_last_error(const char* msg);
 // launchers (rrs_kernels.cu)
 cudaError_t launch_prep(const SlotDev* slots, int nslots, const DsDev* ds, float* z32, double* z64,
                         float* poles, cudaStream_t st);
+// max_ldx: the largest row stride among the tasks' queries (sizes the shared-memory staging)
 cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles_cur,
-                       const double* z64, float* U, double* yz, int round0, cudaStream_t st);
+                       const double* z64, float* U, double* yz, int round0, int max_ldx, cudaStream_t st);
 cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const SlotDev* slots, const DsDev* ds,
                            const float* U, const double* yz, const double* z64, ResDev* res, int64_t* band_out,
                            int* err, cudaStream_t st);
@@ -125,7 +126,8 @@ cudaError_t launch_scatter_dirs(const SlotDev* slots, int nslots, int m, int d, 
 // Per-slot round mode (serving): each slot runs its own next round S.round; poles0 holds the
 // pole of slots at even rounds, poles1 of odd ones; argmin advances S.round.
 cudaError_t launch_gen_slotround(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles0,
-                                 const float* poles1, const double* z64, float* U, double* yz, cudaStream_t st);
+                                 const float* poles1, const double* z64, float* U, double* yz, int max_ldx,
+                                 cudaStream_t st);
 cudaError_t launch_argmin_slotround(SlotDev* slots, const int32_t* slot_list, int nlist, const float* U,
                                    const ResDev* res, float* poles0, float* poles1, cudaStream_t st);
 cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, float alpha, const float* pole,

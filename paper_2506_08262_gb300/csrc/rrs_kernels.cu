@@ -176,42 +176,88 @@ cudaError_t launch_prep(const SlotDev* slots, int nslots, const DsDev* ds, float
 // direction generation: one thread per (slot, direction)
 // ---------------------------------------------------------------------------
 
-__global__ void k_gen(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
-                      const float* __restrict__ poles, const float* __restrict__ poles1,
-                      const double* __restrict__ z64, float* __restrict__ U, double* __restrict__ yz, int round0)
+// One thread per direction of one query (a task never spans queries).  With d <= stage_d the CTA builds
+// its directions in shared memory, transposed (element i of thread t at i * GEN_STRIDE + t: the passes
+// of the generator, the same arithmetic in the same order, touch consecutive banks), and then writes
+// the rows out whole, coalesced; larger d builds each row in place in U.
+constexpr int GEN_NT = 128, GEN_STRIDE = GEN_NT + 1;
+constexpr size_t GEN_STAGE_MAX = 96 * 1024;
+
+__global__ void __launch_bounds__(GEN_NT) k_gen(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
+                                                const float* __restrict__ poles, const float* __restrict__ poles1,
+                                                const double* __restrict__ z64, float* __restrict__ U,
+                                                double* __restrict__ yz, int round0, int stage_d)
 {
+    extern __shared__ float gstage[];
     const TaskDev T = tasks[blockIdx.x];
     const int jl = threadIdx.x;
-    if (jl >= T.nj) return;
     const SlotDev& S = slots[T.slot];
     // launch-wide round, or (round0 < 0) the slot's own round with its pole buffer by parity
     const int rnd = round0 >= 0 ? round0 : S.round;
     const float* pcur = round0 >= 0 ? poles : ((rnd & 1) ? poles1 : poles);
     const int j = T.j0 + jl;
-    float* u = U + S.uoff + (int64_t)j * S.ldx;
     const float ap = alpha_power(S.alpha, rnd);
-    stream_direction(S.seed, (uint32_t)S.qctr, (uint32_t)rnd, (uint32_t)j, S.d, ap, pcur + S.zoff32, u, 1);
-    for (int l = S.d; l < S.ldx; ++l) u[l] = 0.0f;
-    double acc = 0.0;
     const double* z = z64 + S.zoff64;
-    for (int l = 0; l < S.d; ++l) acc = __fma_rn((double)u[l], z[l], acc);
-    yz[S.roff + j] = acc;
+    if (S.d > stage_d) {
+        if (jl >= T.nj) return;
+        float* u = U + S.uoff + (int64_t)j * S.ldx;
+        stream_direction(S.seed, (uint32_t)S.qctr, (uint32_t)rnd, (uint32_t)j, S.d, ap, pcur + S.zoff32, u, 1);
+        for (int l = S.d; l < S.ldx; ++l) u[l] = 0.0f;
+        double acc = 0.0;
+        for (int l = 0; l < S.d; ++l) acc = __fma_rn((double)u[l], z[l], acc);
+        yz[S.roff + j] = acc;
+        return;
+    }
+    if (jl < T.nj) {
+        float* u = gstage + jl;
+        stream_direction(S.seed, (uint32_t)S.qctr, (uint32_t)rnd, (uint32_t)j, S.d, ap, pcur + S.zoff32, u,
+                         GEN_STRIDE);
+        double acc = 0.0;
+        for (int l = 0; l < S.d; ++l) acc = __fma_rn((double)u[l * GEN_STRIDE], z[l], acc);
+        yz[S.roff + j] = acc;
+    }
+    __syncthreads();
+    // rows j0 .. j0 + nj - 1 of this query are contiguous in U
+    float* base = U + S.uoff + (int64_t)T.j0 * S.ldx;
+    const int ldx = S.ldx, total = T.nj * ldx;
+    for (int e = jl; e < total; e += GEN_NT) {
+        const int r = e / ldx, l = e - r * ldx;
+        base[e] = l < S.d ? gstage[l * GEN_STRIDE + r] : 0.0f;
+    }
+}
+
+// directions of up to max_ldx dims are staged in shared memory (up to GEN_STAGE_MAX bytes)
+static cudaError_t gen_launch(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* p0,
+                              const float* p1, const double* z64, float* U, double* yz, int round0, int max_ldx,
+                              cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    int stage_d = max_ldx;
+    const size_t per_dim = sizeof(float) * GEN_STRIDE;
+    if ((size_t)stage_d * per_dim > GEN_STAGE_MAX) stage_d = (int)(GEN_STAGE_MAX / per_dim);
+    const size_t smem = (size_t)stage_d * per_dim;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+    }
+    k_gen<<<ntasks, GEN_NT, smem, st>>>(tasks, slots, p0, p1, z64, U, yz, round0, stage_d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gen(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles_cur,
-                       const double* z64, float* U, double* yz, int round0, cudaStream_t st)
+                       const double* z64, float* U, double* yz, int round0, int max_ldx, cudaStream_t st)
 {
-    if (ntasks <= 0) return cudaSuccess;
-    k_gen<<<ntasks, 128, 0, st>>>(tasks, slots, poles_cur, nullptr, z64, U, yz, round0);
-    return cudaGetLastError();
+    return gen_launch(tasks, ntasks, slots, poles_cur, nullptr, z64, U, yz, round0, max_ldx, st);
 }
 
 cudaError_t launch_gen_slotround(const TaskDev* tasks, int ntasks, const SlotDev* slots, const float* poles0,
-                                 const float* poles1, const double* z64, float* U, double* yz, cudaStream_t st)
+                                 const float* poles1, const double* z64, float* U, double* yz, int max_ldx,
+                                 cudaStream_t st)
 {
-    if (ntasks <= 0) return cudaSuccess;
-    k_gen<<<ntasks, 128, 0, st>>>(tasks, slots, poles0, poles1, z64, U, yz, -1);
-    return cudaGetLastError();
+    return gen_launch(tasks, ntasks, slots, poles0, poles1, z64, U, yz, -1, max_ldx, st);
 }
 
 // y_z = u'z in FP64 for caller-supplied directions (debug path)

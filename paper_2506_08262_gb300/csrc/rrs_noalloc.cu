@@ -278,7 +278,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     for (int l = 0; l < n_refinements; ++l) {
         float* cur = poles + (l & 1) * T;
         float* nxt = poles + ((l + 1) & 1) * T;
-        NA_TRY(launch_gen(gen, nq * gen_per, slots, cur, z64, U, yz, l, st));
+        NA_TRY(launch_gen(gen, nq * gen_per, slots, cur, z64, U, yz, l, ldx, st));
         if (kind == RRS_HALFSPACE)
             NA_TRY(launch_hd_simt(hd, nq * hd_per, ldx, slots, ds, U, yz, z64, res, nullptr, err + 1, st));
         else

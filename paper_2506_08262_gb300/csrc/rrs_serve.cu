@@ -411,7 +411,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         S_TRY(cudaMemcpyAsync(S->d_tab, host.data(), off, cudaMemcpyHostToDevice, S->st));
         char* T = S->d_tab;
         S_TRY(launch_gen_slotround((const TaskDev*)(T + o_gen), (int)gen.size(), S->d_slots, S->d_p0, S->d_p1,
-                                   S->d_z64, S->d_U, S->d_yz, S->st));
+                                   S->d_z64, S->d_U, S->d_yz, S->max_ldx, S->st));
         S_TRY(launch_hd_simt((const TaskDev*)(T + o_hd), (int)hd.size(), S->max_ldx, S->d_slots, S->d_ds, S->d_U,
                              S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err, S->st));
         for (auto& to : o_tc)
