@@ -243,7 +243,8 @@ uint64_t rrs_launch_count(rrs_ctx* ctx);
 #define RRS_STAGE_HD_TC 3     /* halfspace counts, tcgen05 split-BF16x3 projection */
 #define RRS_STAGE_PDAP 4      /* projection / asymmetric projection depth (selection) */
 #define RRS_STAGE_ARGMIN 5    /* round minimum and pole update (Alg. 1 steps 4-6) */
-#define RRS_NSTAGES 6
+#define RRS_STAGE_KEYS 6      /* selection keys formed once per round (d > 16, or n beyond shared memory) */
+#define RRS_NSTAGES 7
 
 /*
  * rrs_profile_enable - turn per-stage timing on (on != 0) or off and reset the

@@ -105,7 +105,7 @@ _SIGS = {
                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
 }
 
-RRS_STAGES = ("prep", "gen", "hd_simt", "hd_tc", "pdap", "argmin")
+RRS_STAGES = ("prep", "gen", "hd_simt", "hd_tc", "pdap", "argmin", "keys")
 
 
 def exported_symbols():

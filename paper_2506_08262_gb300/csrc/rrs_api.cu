@@ -467,13 +467,17 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
             const int total = P.n_pd[c][l], chunk = P.pd_keys_chunk[c];
             for (int t0 = 0; t0 < total; t0 += chunk) {
                 const int cnt = std::min(chunk, total - t0);
+                {
+                    StageTimer t(ctx, RRS_STAGE_KEYS, st, capturing);
+                    CUDA_TRY(launch_pdap_keys(P.d_pd[c] + t0, cnt, P.pd_group[c], P.d_slots, P.d_ds,
+                                              P.ds[P.pd_keys_ds[c]], P.U, P.keys, st));
+                }
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
-                CUDA_TRY(launch_pdap_keys(P.d_pd[c] + t0, cnt, P.pd_group[c], P.d_slots, P.d_ds, P.ds[P.pd_keys_ds[c]],
-                                          P.U, P.keys, st));
                 CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
                                      P.d_ds, P.U, P.z32, P.res, ctx->d_err, st, P.keys));
                 ctx->launches += 2;
-                ctx->stage_launches[RRS_STAGE_PDAP] += 2;
+                ctx->stage_launches[RRS_STAGE_KEYS]++;
+                ctx->stage_launches[RRS_STAGE_PDAP]++;
             }
         }
         if (P.n_arg[l] > 0) {
