@@ -38,3 +38,19 @@ def test_status_strings_and_no_gpu_error():
     with pytest.raises(rrs.RRSError) as e:
         rrs.rrs_create(0)
     assert e.value.status in (rrs.RRS_ERR_CUDA, rrs.RRS_ERR_INVALID_ARG)
+
+
+def test_binding_constants_match_the_header():
+    # the binding restates the header's numeric constants; a drift would silently misread profiler slots,
+    # statuses or request fields
+    text = open(os.path.join(ROOT, "include", "rrs.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(RRS_\w+)\s+\(?(-?\d+)u?\)?", text)}
+    stages = sorted((v, k) for k, v in defines.items() if k.startswith("RRS_STAGE_"))
+    assert [v for v, _ in stages] == list(range(defines["RRS_NSTAGES"]))
+    assert len(rrs.RRS_STAGES) == defines["RRS_NSTAGES"]
+    for v, k in stages:
+        assert rrs.RRS_STAGES[v] == k[len("RRS_STAGE_"):].lower(), (k, rrs.RRS_STAGES[v])
+    for k, v in defines.items():
+        if k.startswith(("RRS_ERR_", "RRS_PREC_", "RRS_F32", "RRS_F64", "RRS_HALFSPACE", "RRS_PROJECTION",
+                         "RRS_ASYM_PROJECTION")) and hasattr(rrs, k):
+            assert getattr(rrs, k) == v, k
