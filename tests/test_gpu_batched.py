@@ -95,6 +95,27 @@ def test_batched_mixes_outside_and_resident_keys(ctx):
         ctx.free(did)
 
 
+def test_batched_mixes_staged_and_in_place_directions(ctx):
+    # one launch generates d = 10 directions in shared memory and d = 200 ones in place in device memory
+    problems = []
+    for i, (n, d, kind) in enumerate([(400, 200, 0), (900, 10, 1), (500, 200, 2), (700, 10, 0)]):
+        X, Z = workloads.gaussian_cloud(250 + i, n, d, 4, dtype=np.float32)
+        problems.append(workloads.Problem(X, Z, kind, 60, 3, 0.8, 0))
+    reqs, outs, ids = make_requests(ctx, problems)
+    stream = torch.cuda.current_stream()
+    rrs.rrs_depth_batched(ctx.handle, reqs, use_graph=False, stream=stream)
+    rrs.rrs_check(ctx.handle, stream)
+    for i, P in enumerate(problems):
+        d, c, b, ch = alone(ctx, ids[i], P, P.r, P.seed + i, outs[i]["Z"])
+        np.testing.assert_array_equal(outs[i]["depth"].cpu().numpy(), d)
+        np.testing.assert_array_equal(outs[i]["best"].cpu().numpy(), b)
+        np.testing.assert_array_equal(outs[i]["choice"].cpu().numpy(), ch)
+        if P.kind == 0:
+            np.testing.assert_array_equal(outs[i]["count"].cpu().numpy(), c)
+    for did in ids:
+        ctx.free(did)
+
+
 def test_batched_against_oracle_sample(ctx):
     problems = workloads.c4(seed=43, n_datasets=6, n_lo=100, n_hi=2000, q_hi=6, scale=1.0)
     for P in problems:

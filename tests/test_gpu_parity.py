@@ -315,6 +315,14 @@ def test_projection_depth_lattice_ties(ctx, kind, n):
     assert_follow(g, X, Z, kind, 24, 2, 0.7, 9)
 
 
+def test_halfspace_beyond_the_direction_stage(ctx):
+    # d = 200: directions wider than the generator's shared-memory stage are built in place in device
+    # memory; counts, depths and best indices still bit-exact
+    X, Z = workloads.gaussian_cloud(41, 300, 200, 3, dtype=np.float32)
+    g = gpu_rrs(ctx, X, Z, H, 40, 2, 0.6, 3)
+    assert_hd_exact(g, oracle.rrs(X, Z, H, 40, 2, 0.6, 3))
+
+
 def test_zero_queries_is_a_no_op(ctx):
     X = np.ones((4, 2), np.float32)
     did = rrs.rrs_register_dataset(ctx.handle, X, 4, 2, rrs.RRS_F32, False)
