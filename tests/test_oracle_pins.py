@@ -253,6 +253,22 @@ def test_univariate_exact_invariances(kind):
     assert oracle.univariate(kind, X, z, u * np.float32(4.0)) == base
 
 
+@pytest.mark.parametrize("kind", [H, P, AP])
+def test_rrs_translation_invariance_exact(kind):
+    # depth is translation invariant (Sec. 2: every univariate depth sees y - y_z or y - med).  With small
+    # integer data, an integer shift and FP32 directions every FP64 product and sum is exact, so the whole
+    # search (same directions, same decisions) must return identical results
+    rng = np.random.default_rng(30 + kind)
+    X = rng.integers(-20, 21, size=(257, 3)).astype(np.float64)
+    Z = rng.integers(-10, 11, size=(6, 3)).astype(np.float64)
+    c = np.array([37.0, -12.0, 5.0])
+    a = oracle.rrs(X, Z, kind, 90, 3, 0.6, 4)
+    b = oracle.rrs(X + c, Z + c, kind, 90, 3, 0.6, 4)
+    np.testing.assert_array_equal(a["depth"], b["depth"])
+    np.testing.assert_array_equal(a["count"], b["count"])
+    np.testing.assert_array_equal(a["best"], b["best"])
+
+
 def test_asymmetric_depth_is_not_symmetric():
     # D_AP(z|X along u) != D_AP(-z|-X along u) in general (Supp. A symmetry fails)
     X = np.array([[0.0], [1.0], [1.0], [10.0], [11.0]])
