@@ -4,6 +4,7 @@ The path shards by query with no data exchange, so N GPUs run N replicas; the
 benchmark's only cross-rank step is taking the slowest rank's time and scaling
 the work by N.  These tests run that logic on two gloo ranks.
 """
+import json
 import os
 import socket
 import subprocess
@@ -61,3 +62,22 @@ def test_reference_arm_only_rank0_runs(tmp_path):
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_carries_the_contract_keys():
+    # the oracle arm on the host cores: one JSON line with the metric, a cpu_baseline describing the run and
+    # an e2e object without host-device copies
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    assert line["value"] > 0 and line["unit"] == "query-depths/s" and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("projection + asymmetric projection depth")
