@@ -13,6 +13,14 @@ query-depths per second (and point-direction projections per second).
 bounded sample of the same workload per step).  For N > 1 (torchrun) every
 rank runs its own replica of the workload (weak scaling; the path needs no
 data exchange) and the slowest rank's time is reported.
+
+Other workloads (``--workload``, one GPU): ``c3`` halfspace depth at d = 50 on
+the tensor cores against the FP32 path; ``c4`` 256 datasets in one batched,
+graph-captured launch sequence; ``c5`` continuous-batching serving with p50 /
+p99 latency (``--sweep`` for a rate sweep); ``grid`` the paper's per-point
+timing grid (its Tables 1 and 2); ``ranks`` its center-outward ranking
+correlations at n = 100,000 (Tables 4 and 5); ``convergence`` its
+cap-shrinkage study (Sec. 5.1).
 """
 from __future__ import annotations
 
