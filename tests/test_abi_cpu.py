@@ -54,3 +54,35 @@ def test_binding_constants_match_the_header():
         if k.startswith(("RRS_ERR_", "RRS_PREC_", "RRS_F32", "RRS_F64", "RRS_HALFSPACE", "RRS_PROJECTION",
                          "RRS_ASYM_PROJECTION")) and hasattr(rrs, k):
             assert getattr(rrs, k) == v, k
+
+
+def test_the_product_path_and_the_oracle_stay_apart():
+    # the oracle is test infrastructure: the CUDA library and its binding never reference it, the oracle never
+    # references the library, and bench.py touches it only in its CPU-baseline and reference-arm functions
+    import ast
+
+    pkg = os.path.join(ROOT, "paper_2506_08262_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b", text), os.path.join(dirpath, f)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            code = re.sub(r'""".*?"""|/\*.*?\*/|#[^\n]*', "", text, flags=re.S)
+            assert "paper_2506_08262_gb300" not in code and "csrc" not in code and "rrs_device" not in code, f
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    users = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, (ast.Import, ast.ImportFrom)):
+                    names = [a.name for a in node.names] + ([node.module] if isinstance(node, ast.ImportFrom) else [])
+                    if any(n and n.split(".")[0] == "oracle" for n in names):
+                        users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any(a.name.split(".")[0] == "oracle" for n in top for a in n.names)
+    assert users == {"oracle_sample_rate", "run_reference"}, users
