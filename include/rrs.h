@@ -69,7 +69,7 @@ rrs_status rrs_create(rrs_ctx** out, int32_t device, uint64_t hbm_budget_bytes);
 
 /* rrs_destroy - free every dataset and workspace of the context, then the
  * context.  NULL is accepted.  Work already queued by the context is
- * synchronised first. */
+ * synchronised first.  Always returns RRS_OK. */
 rrs_status rrs_destroy(rrs_ctx* ctx);
 
 /*
@@ -199,8 +199,12 @@ const char* rrs_last_error(void);
  * rrs_debug_directions - write the m directions of round `round` (1-based)
  * for query counter q into U (m x d FP32, row-major, device pointer), drawn
  * around `pole` (d FP32, device pointer; ignored for round 1) with the
- * library's generator.  Lets tests compare the device direction stream bit
- * for bit with an independent implementation.  Synchronous.
+ * library's generator: Alg. S1 (uniform on the sphere) for round 1, Alg. S4
+ * (a cap of angle (pi/2) cap_shrink^(round-1) around the pole) after.  Lets
+ * tests compare the device direction stream bit for bit with an independent
+ * implementation.  U and pole stay owned by the caller.  Synchronous.
+ * Errors: INVALID_ARG (NULL U, m < 0, d < 1, round < 1, q < 0, no pole for
+ * round > 1), CUDA.
  */
 rrs_status rrs_debug_directions(rrs_ctx* ctx, uint64_t seed, int32_t q, int32_t round, int32_t m,
                                 int32_t d, double cap_shrink, const float* pole, float* U);
@@ -212,7 +216,12 @@ rrs_status rrs_debug_directions(rrs_ctx* ctx, uint64_t seed, int32_t q, int32_t 
  * device).  depth_out (n_queries x m, device) receives D(u'z | u'X);
  * count_out (n_queries x m, device, halfspace only, may be NULL) receives
  * min(#<=, #>=); band_out (n_queries x m, device, halfspace only, may be
- * NULL) receives how many points fell in the near-tie band.  Synchronous.
+ * NULL) receives how many points fell in the near-tie band.  The univariate
+ * depths are those of Sec. 2 (D_H, D_P, D_AP), computed by the same kernels
+ * as rrs_depth.  All buffers stay owned by the caller.  Synchronous.
+ * Errors: INVALID_ARG (NULL buffers, n_queries < 1, m < 1), NOT_FOUND,
+ * UNSUPPORTED and BUDGET as rrs_depth, CUDA, and INTERNAL / TIMEOUT for
+ * failures flagged on the device.
  */
 rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* Z,
                                   int64_t n_queries, int32_t dtype, int32_t kind, int32_t m,
@@ -220,9 +229,11 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
                                   int64_t* count_out, int64_t* band_out);
 
 /* rrs_check - wait for `stream` (a cudaStream_t, NULL = legacy default) and
- * report device-side failures flagged by earlier stream-ordered calls
- * (INTERNAL), clearing the flags.  Use it after rrs_depth with device outputs
- * or rrs_depth_batched. */
+ * report device-side failures flagged by earlier stream-ordered calls,
+ * clearing the flags.  Use it after rrs_depth with device outputs or
+ * rrs_depth_batched.  Errors: INVALID_ARG (NULL context), CUDA, INTERNAL (an
+ * invariant failed on the device, e.g. a selection that did not converge),
+ * TIMEOUT (a bounded device wait gave up). */
 rrs_status rrs_check(rrs_ctx* ctx, void* stream);
 
 /*
@@ -230,6 +241,7 @@ rrs_status rrs_check(rrs_ctx* ctx, void* stream);
  * waits: one thread waits on an mbarrier that nothing completes, gives up after
  * limit_cycles SM clock cycles and flags a timeout.  Returns RRS_ERR_TIMEOUT
  * (the expected outcome) with the context left usable.  Synchronous.
+ * Errors besides: INVALID_ARG (NULL context, limit_cycles < 0), CUDA.
  */
 rrs_status rrs_debug_wait_timeout(rrs_ctx* ctx, int64_t limit_cycles);
 
@@ -250,7 +262,7 @@ uint64_t rrs_launch_count(rrs_ctx* ctx);
  * rrs_profile_enable - turn per-stage timing on (on != 0) or off and reset the
  * accumulated figures.  While on, every launch of rrs_depth /
  * rrs_depth_batched (outside graph capture) is bracketed by two CUDA events
- * recorded on the launching stream.
+ * recorded on the launching stream.  Errors: INVALID_ARG (NULL context).
  */
 rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on);
 
@@ -258,7 +270,7 @@ rrs_status rrs_profile_enable(rrs_ctx* ctx, int32_t on);
  * rrs_profile_read - wait for the recorded events and return, per stage, the
  * accumulated device milliseconds (ms_out[RRS_NSTAGES], host) and launch
  * counts (launches_out[RRS_NSTAGES], host, may be NULL) since the last
- * rrs_profile_enable.
+ * rrs_profile_enable.  Errors: INVALID_ARG (NULL context or ms_out), CUDA.
  */
 rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out);
 
@@ -307,6 +319,8 @@ rrs_status rrs_server_submit(rrs_server* server, int64_t dataset_id, const void*
  * retire finished requests (their host copies are enqueued on the stream).
  * Returns after enqueueing.  *active_queries_out / *pending_requests_out
  * (optional) receive the queries in flight and the requests still waiting.
+ * Each step is one refinement round (Alg. 4) for every active query, at that
+ * query's own round.  Errors: INVALID_ARG (NULL server), CUDA.
  */
 rrs_status rrs_server_step(rrs_server* server, int32_t* active_queries_out, int32_t* pending_requests_out);
 
@@ -314,7 +328,8 @@ rrs_status rrs_server_step(rrs_server* server, int32_t* active_queries_out, int3
  * buffer (the request is then forgotten), else 0.  Errors: NOT_FOUND, CUDA. */
 rrs_status rrs_server_poll(rrs_server* server, int64_t request_id, int32_t* done_out);
 
-/* rrs_server_destroy - wait for the stream, drop queued requests, free the pool. */
+/* rrs_server_destroy - wait for the stream, drop queued requests, free the pool.
+ * NULL is accepted.  Always returns RRS_OK. */
 rrs_status rrs_server_destroy(rrs_server* server);
 
 /*
