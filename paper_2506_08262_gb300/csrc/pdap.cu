@@ -6,9 +6,9 @@
 // shared memory, or, when n is beyond what shared memory holds, G = 2
 // directions whose keys stay outside: formed once by a keys kernel and read
 // from global memory at every pass, or (allocation-free entry point)
-// recomputed from X at every pass; the arithmetic is the same throughout, so
-// are the values.  The whole CTA projects (pass A: every
-// point on the G directions, keys stored, each added to a 2048-bucket histogram over
+// recomputed from X at every pass; the arithmetic is the same throughout, and
+// so are the values.  The whole CTA projects (pass A: every point on the G
+// directions, keys stored, each added to a 2048-bucket histogram over
 // u'c +- 5 sigma_u, bucket = monotone FP32 map of the key).  Then the CTA
 // splits into G groups of (CTA threads)/G, one per direction, each synchronising
 // on its own named barrier, so the directions never wait for one another:
