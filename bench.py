@@ -515,6 +515,44 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+def roofline_mix(prof, problems, bf16_peak):
+    """Per-stage rooflines of one profiled batched call and their time-weighted mix: each stage's algorithmic
+    work over the requests that reach it, divided by the stage's device time, against that stage's peak."""
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12      # TFLOP/s (FMA = 2)
+    alu = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12           # T ops/s
+    work = {"hd_tc": 0.0, "hd_simt": 0.0, "keys": 0.0, "pdap": 0.0}
+    for P in problems:
+        pairs = float(P.nq) * P.r * P.m * P.n
+        if P.kind == workloads.HALFSPACE:
+            if P.d + 2 <= 128:
+                work["hd_tc"] += 6.0 * P.d * pairs
+            else:
+                work["hd_simt"] += 2.0 * P.d * pairs
+        else:
+            keys = P.d > 16 or P.n > 55_000   # keys formed by their own kernel
+            if keys:
+                work["keys"] += 2.0 * P.d * pairs
+            work["pdap"] += (alu_ops_per_element(P.kind, P.d) - (P.d if keys else 0)) * pairs
+    peaks = {"hd_tc": (bf16_peak, "TFLOP/s"), "hd_simt": (fp32, "TFLOP/s"), "keys": (fp32, "TFLOP/s"),
+             "pdap": (alu, "Top/s")}
+    stages, num, den = {}, 0.0, 0.0
+    for name, w in work.items():
+        ms = prof.get(name, (0.0, 0))[0]
+        if w <= 0 or ms <= 0:
+            continue
+        achieved = w / (ms / 1000) / 1e12
+        peak, unit = peaks[name]
+        stages[name] = {"ms": ms, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak}
+        num += achieved / peak * ms
+        den += ms
+    other = sum(v[0] for k, v in prof.items() if k not in stages)
+    return {"stages": stages, "time_weighted_frac": num / den if den else None, "other_stages_ms": other,
+            "how": "one profiled batched call (no graph); algorithmic work per stage / stage device time; "
+                   "halfspace 6d FLOP per pair against the sustained BF16 peak, keys 2d FLOP per pair against "
+                   "the FP32 FMA peak, selection d+6 (+2 for D_AP; without the d projection FMAs when keys come "
+                   "from the keys kernel) ops per pair against the ALU peak"}
+
+
 WORKLOAD_C4 = ("batched: 256 datasets, n log-uniform [500, 50000], d uniform {5..100}, N(mu_k, Sigma_k), "
                "1..1000 queries each, kind uniform over halfspace/projection/asymmetric, k=1000 over r=10, "
                "alpha=0.9, FP32")
@@ -609,6 +647,19 @@ def run_c4(args):
             "one_call_per_request_fp32": {"ms_per_step": ms_s, "value": total_q / (ms_s / 1000)},
             "speedup_batched_over_per_request": ms_s / ms_b, "speedup_tensor_cores_in_batch": ms_f / ms_b,
             "results_identical": bool(same), "clocks": clocks}
+    # per-stage rooflines of the tensor-core batch (one extra call, timed by the library's stage profiler)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    rrs.rrs_profile_enable(ctx, True)
+    rrs.rrs_depth_batched(ctx, reqs_tc, use_graph=False, stream=stream)
+    torch.cuda.synchronize()
+    prof = rrs.rrs_profile_read(ctx)
+    rrs.rrs_profile_enable(ctx, False)
+    rrs.rrs_check(ctx, stream)
+    line["roofline_mix"] = roofline_mix(prof, problems, float(peaks.get("bf16_tflops_sustained", 1700.0)))
     for did, _, _, _ in keep:
         rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
