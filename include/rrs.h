@@ -351,15 +351,19 @@ rrs_status rrs_server_destroy(rrs_server* server);
  *      uses stream counter q, so results equal rrs_depth's bit for bit.
  *   depth_out (n_queries doubles) and count_out (n_queries int64, halfspace
  *      counts, or -1; may be NULL): device pointers.
- *   stream: cudaStream_t (NULL = legacy default stream).  The call returns
- *      after the stream has finished its work.
+ *   stream: cudaStream_t (NULL = legacy default stream).  The call waits for
+ *      the stream twice (it reads the input check and the device-side error
+ *      flags back to the host) and returns after the stream has finished its
+ *      work.
  * Limits: everything the call needs (about 4*(n+1)*(d+4) bytes for X plus
  * about n_queries * m * 4*(d+10) bytes for the rounds, m = ceil(k/r)) must fit
  * in RRS_NOALLOC_SCRATCH_BYTES; a larger request is rejected with
  * RRS_ERR_BUDGET and a message giving both sizes (rrs_last_error).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * Every call looks up the array's device address (cudaGetSymbolAddress) with
+ * the calling device current, so a device reset cannot leave a stale address.
+ * The first call on a device also loads the library's device code there;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the
  * last call's contents (each call clears what must start at zero); calls
  * whose GPU work overlaps -- other streams or other host threads -- race on
  * it and must be serialised by the caller.

@@ -216,7 +216,38 @@ def rrs_depth_noalloc(X, n: int, d: int, dtype: int, Z, n_queries: int, kind: in
                       stream=None) -> None:
     """For callers that cannot allocate device memory: all working memory comes from the
     library's fixed device array (RRS_NOALLOC_SCRATCH_BYTES); X, Z and the outputs are
-    device pointers; calls must not overlap on the GPU."""
+    device pointers; calls must not overlap on the GPU.
+
+    The C entry point takes raw device addresses and cannot tell a host buffer, a short
+    buffer or a buffer of the wrong element type from a good one, so this wrapper checks
+    every tensor it forwards (CUDA, on the current device, contiguous, dtype and length)
+    and raises RRSError(RRS_ERR_INVALID_ARG) before anything reaches the GPU."""
+    import torch
+
+    def bad(why):
+        raise RRSError(RRS_ERR_INVALID_ARG, f"rrs_depth_noalloc: {why}")
+
+    if dtype not in (RRS_F32, RRS_F64):
+        bad(f"unknown dtype code {dtype}")
+    want = torch.float32 if dtype == RRS_F32 else torch.float64
+    cur = torch.cuda.current_device()
+    for name, t, tdt, need in (("X", X, want, n * d), ("Z", Z, want, n_queries * d),
+                               ("depth_out", depth_out, torch.float64, n_queries),
+                               ("count_out", count_out, torch.int64, n_queries)):
+        if t is None:
+            if name == "count_out":
+                continue
+            bad(f"{name} is missing")
+        if not isinstance(t, torch.Tensor):
+            bad(f"{name} must be a CUDA tensor, got {type(t).__name__}")
+        if not t.is_cuda or t.device.index != cur:
+            bad(f"{name} must live on the current CUDA device {cur}, got {t.device}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+        if t.dtype != tdt:
+            bad(f"{name} must be {tdt}, got {t.dtype}")
+        if t.numel() < need:
+            bad(f"{name} holds {t.numel()} elements, needs {need}")
     _check(load().rrs_depth_noalloc(_ptr(X), n, d, dtype, _ptr(Z), n_queries, kind, n_dirs, n_refinements,
                                     float(cap_shrink), seed, _ptr(depth_out), _ptr(count_out), _stream(stream)),
            "rrs_depth_noalloc")

@@ -52,13 +52,15 @@ struct Ctl {
     float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: about (y - lo_b) * sc_y
     float off_y[MAXG];                 // -lo_b * sc_y (bucket_fma offset)
     float scale[MAXG];                 // sigma_u (or the radius) of each direction
-    float yz[MAXG];
     int red[MAXG][NWARP];
     float fred[MAXG][2 * NWARP];
     int fill[MAXG][2];
     int f_b1[MAXG], f_c1[MAXG], f_b2[MAXG], f_c2[MAXG];   // bucket search results
     float pv1[MAXG], pv2[MAXG];                           // rank pick results
+    int pi1[MAXG], pi2[MAXG];                             // their point indices
     int gn[MAXG];
+    int gi[MAXG];                                         // smallest index of a tied run (fallback)
+    double y64[MAXG][4];                                  // FP64 projections of the selected points
 };
 
 template <int GS>
@@ -188,38 +190,97 @@ __device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, Ctl& 
     q.sync();
 }
 
-// Values of the 0-based ranks s1 <= s2 among buf[0..cnt), by the group.
+// Values and point indices of the 0-based ranks s1 <= s2 among the pairs (buf, ib)[0..cnt), ordered by
+// value and then by point index, by the group.  The indices of one buffer are distinct, so every rank
+// names one pair and the choice among equal values never depends on the gather order.
 template <int GS>
-__device__ void gpick(const Grp<GS>& q, const float* buf, int cnt, int s1, int s2, Ctl& C, float& o1, float& o2)
+__device__ void gpick(const Grp<GS>& q, const float* buf, const int* ib, int cnt, int s1, int s2, Ctl& C, float& o1,
+                      float& o2, int& i1, int& i2)
 {
     for (int t = q.t; t < cnt; t += GS) {
         const float v = buf[t];
-        int nlt = 0, nle = 0;
+        const int iv = ib[t];
+        int r = 0;
         for (int s = 0; s < cnt; ++s) {
             const float w2 = buf[s];
-            nlt += (w2 < v);
-            nle += (w2 <= v);
+            r += (w2 < v) | ((w2 == v) & (ib[s] < iv));
         }
-        if (nlt <= s1 && s1 < nle) C.pv1[q.g] = v;
-        if (nlt <= s2 && s2 < nle) C.pv2[q.g] = v;
+        if (r == s1) {
+            C.pv1[q.g] = v;
+            C.pi1[q.g] = iv;
+        }
+        if (r == s2) {
+            C.pv2[q.g] = v;
+            C.pi2[q.g] = iv;
+        }
     }
     q.sync();
     o1 = C.pv1[q.g];
     o2 = C.pv2[q.g];
+    i1 = C.pi1[q.g];
+    i2 = C.pi2[q.g];
+    q.sync();
+}
+
+// Inclusive prefix sums of h[0..NB) in place, by the group.
+template <int GS>
+__device__ void gprefix(const Grp<GS>& q, unsigned* h, Ctl& C)
+{
+    constexpr int PER = NB / GS;
+    const int lane = q.t & 31, w = q.t >> 5;
+    unsigned v[PER];
+    uint4* h4 = reinterpret_cast<uint4*>(h + q.t * PER);
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k) {
+        const uint4 a = h4[k];
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 1; k < PER; ++k) v[k] += v[k - 1];
+    int incl = (int)v[PER - 1];
+    const int own = incl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) C.red[q.g][w] = incl;
+    q.sync();
+    int base = incl - own;
+    for (int i = 0; i < w; ++i) base += C.red[q.g][i];
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k)
+        h4[k] = make_uint4(v[4 * k] + base, v[4 * k + 1] + base, v[4 * k + 2] + base, v[4 * k + 3] + base);
     q.sync();
 }
 
 // Generic exact selection of ranks q1 <= q2 over one direction's values f(0..L-1),
-// all in [lo, hi], by iterated bucketing (the fallback path); hist and buf are the
-// direction's own areas.
+// all in [lo, hi], by iterated bucketing (the fallback path); hist, buf and ibuf are the
+// direction's own areas.  Returns the values and the point indices of the two ranks.
 template <int GS, class F>
 __device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, float hi, unsigned* hist, float* buf,
-                        Ctl& C, float& v1, float& v2, int* err)
+                        int* ibuf, Ctl& C, float& v1, float& v2, int& i1, int& i2, int* err)
 {
     int below = 0;
     for (int iter = 0; iter < 24; ++iter) {
         if (!(lo < hi)) {
+            // every remaining candidate equals lo: both ranks hold that value, taken at the
+            // smallest point index that holds it
+            if (q.t == 0) C.gi[q.g] = 0x7FFFFFFF;
+            q.sync();
+            for (int i = q.t; i < L; i += GS) {
+                if (f(i) == lo) {
+                    atomicMin(&C.gi[q.g], i);
+                    break;
+                }
+            }
+            q.sync();
             v1 = v2 = lo;
+            i1 = i2 = C.gi[q.g];
+            q.sync();
             return;
         }
         float scale = __fdiv_rn((float)FB_NB, __fsub_rn(hi, lo));
@@ -243,12 +304,15 @@ __device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, 
                     const int b = bucket(a, lo, scale);
                     if (b >= b1 && b <= b2) {
                         const int pos = atomicAdd(&C.gn[q.g], 1);
-                        if (pos < FB_CAP) buf[pos] = a;
+                        if (pos < FB_CAP) {
+                            buf[pos] = a;
+                            ibuf[pos] = i;
+                        }
                     }
                 }
             }
             q.sync();
-            gpick(q, buf, cnt, q1 - below - c1, q2 - below - c1, C, v1, v2);
+            gpick(q, buf, ibuf, cnt, q1 - below - c1, q2 - below - c1, C, v1, v2, i1, i2);
             return;
         }
         float nlo = FLT_MAX, nhi = -FLT_MAX;
@@ -267,6 +331,7 @@ __device__ void gselect(const Grp<GS>& q, F f, int L, int q1, int q2, float lo, 
     }
     if (q.t == 0) atomicOr(err, ERR_SELECT_ITER);
     v1 = v2 = __int_as_float(0x7FC00000);
+    i1 = i2 = -1;
 }
 
 // 1 / (1 + num / spread) = spread / (spread + num) for num, spread >= 0 (FP64 inputs, exact differences
@@ -347,27 +412,56 @@ struct KeysRecomputed {
     __device__ __forceinline__ float4 get4(int i) const { return make_float4(get(i), get(i + 1), get(i + 2), get(i + 3)); }
 };
 
+// FP64 projection u'x_i of point i: one sequential FMA chain over the dims, from the FP64 rows when
+// the data came in FP64 (the direction generator forms the query's y_z = u'z the same way, so a query
+// equal to a data point projects to the same value).  Every product of an FP32 direction component and
+// an FP32 (or FP64) coordinate is rounded at most once per added term.
+__device__ __forceinline__ double proj64(const DsDev& D, const float* u, int i)
+{
+    double acc = 0.0;
+    if (D.X64) {
+        const double* xr = D.X64 + (int64_t)i * D.d;
+        for (int l = 0; l < D.d; ++l) acc = __fma_rn((double)u[l], xr[l], acc);
+    } else {
+        const float* xr = D.X32 + (int64_t)i * D.ldx;
+        for (int l = 0; l < D.d; ++l) acc = __fma_rn((double)u[l], (double)xr[l], acc);
+    }
+    return acc;
+}
+
 // Exact median / MAD / MAD_+ of one direction's keys y (after the projection pass) and the
-// depth, by its group q of GS threads.
+// depth, by its group q of GS threads.  The selection runs on the FP32 keys and yields the points
+// holding the wanted order statistics (ties broken by point index); the depth is then formed from
+// FP64 projections of those few points and the FP64 y_z (yzv).
+//   median  the bucket run of ranks k1, k2 (from the key histogram H) is gathered and ranked;
+//   D_P     in the same gather pass, two runs L, R placed symmetrically about the median run at the
+//           bucket distance where the window count reaches the MAD rank; after the median is known
+//           their deviations are ranked, and the result is accepted only when every key between the
+//           runs deviates no more and every key outside no less than the picked values (else a
+//           |y - med| histogram pass decides);
+//   D_AP    in the same gather pass, the run of the MAD_+ ranks guessed for no key tying the median.
+// Runs that overflow the gather buffer fall back to iterated bucket selection.
 template <int GS, class K>
-__device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C, unsigned* H, float* B0, int n,
-                                           bool ap, const DsDev& D, int64_t roff, ResDev* __restrict__ res, int* err)
+__device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C, unsigned* H, float* B0, int* I0,
+                                           int n, bool ap, const float* u, const DsDev& D, double yzv, int64_t roff,
+                                           ResDev* __restrict__ res, int* err)
 {
     const int g = q.g;
-    float* B1 = B0 + CAP;                      // MAD_+ guess run (D_AP) or MAD run (D_P); B0 holds the median run
+    float* B1 = B0 + CAP;   // MAD_+ guess run (D_AP) or the L, R runs (D_P); B0 holds the median run
+    int* I1 = I0 + CAP;
     const float sc = C.sc_y[g], of = C.off_y[g];
     const int k1 = (n - 1) / 2, k2 = n / 2;
     const int n4 = n & ~3;
     const float qnan = __int_as_float(0x7FC00000);
+    constexpr int OFF = 1 << 30;   // a run start no bucket test can reach
 
-    // bucket runs of the median ranks and (D_AP) of the MAD_+ ranks under the guess that no
-    // key ties the median
     int ba, ca, bb, cb;
     gfind(q, H, k1, k2, C, ba, ca, bb, cb);
     const int c_lo0 = ca, cnt0 = cb + (int)H[bb] - ca;
     int fb = cnt0 > CAP ? 1 : 0;   // 1: fall back for every statistic, 2: only for the spread
+    // second gathered set: buckets b with |2b - c2| in [dl2, dl2 + dw2]
+    int c2 = 0, dl2 = OFF, dw2 = 0, c_lo1 = 0, cnt1 = 0, c_in = 0;
     const int npos_guess = (n & 1) ? (n - 1) / 2 : n / 2;
-    int c_lo1 = 0, cnt1 = 0, bl1 = 1 << 30, bw1 = 0;
     if (ap && npos_guess > 0) {
         const int base = n - npos_guess;
         int b3, c3, b4, c4;
@@ -375,39 +469,76 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
         c_lo1 = c3;
         cnt1 = c4 + (int)H[b4] - c3;
         if (cnt1 > CAP) fb = 1;
-        bl1 = b3;
-        bw1 = b4 - b3;
+        c2 = 2 * b3 + (b4 - b3);   // the run [b3, b4]
+        dl2 = 0;
+        dw2 = b4 - b3;
+    } else if (!ap && !fb) {
+        gprefix(q, H, C);   // H: inclusive prefix counts from here on (the fallbacks rebuild it)
+        // smallest s with more than k2 keys in the buckets [ba - s, bb + s]
+        if (q.t == 0) C.f_b1[g] = NB;
+        q.sync();
+        constexpr int PER = NB / GS;
+#pragma unroll 1
+        for (int k = 0; k < PER; ++k) {
+            const int s = q.t * PER + k;
+            const int hi = bb + s < NB - 1 ? bb + s : NB - 1, lo = ba - s;
+            const int c = (int)H[hi] - (lo >= 1 ? (int)H[lo - 1] : 0);
+            if (c > k2) {
+                atomicMin(&C.f_b1[g], s);
+                break;
+            }
+        }
+        q.sync();
+        const int ss = C.f_b1[g];
+        q.sync();
+        // keys deviating by about the MAD sit within w + 1 buckets of distance ss from the median run
+        const int w = bb - ba + 1;
+        const int L0 = ba - ss - w - 1, L1 = ba - ss + w + 1, R0 = bb + ss - w - 1, R1 = bb + ss + w + 1;
+        if (ss >= w + 2 && L0 >= 1 && R1 <= NB - 2) {
+            const int cl = (int)(H[L1] - H[L0 - 1]) + (int)(H[R1] - H[R0 - 1]);
+            if (cl <= CAP) {
+                cnt1 = cl;
+                c_in = (int)(H[R0 - 1] - H[L1]);
+                c2 = ba + bb;
+                dl2 = 2 * ss - w - 3;
+                dw2 = 4 * w + 4;
+            }
+        }
     }
     float m1 = qnan, m2 = qnan, p1 = 0.f, p2 = 0.f;
+    int im1 = -1, im2 = -1, ip1 = -1, ip2 = -1;
     int npos = 0;
     if (!fb) {
         if (q.t < 2) C.fill[g][q.t] = 0;
-        if (q.t == 0) C.pv1[g] = C.pv2[g] = qnan;
         q.sync();
-        // a run that is off gets a start no bucket index can reach
         const int bl0 = ba, bw0 = bb - ba;
-        if (!ap) bl1 = 1 << 30;
-        auto gather = [&](float v) {
+        auto gather = [&](float v, int i) {
             const int b = bucket_fma(v, sc, of);
             if ((unsigned)(b - bl0) <= (unsigned)bw0) {
                 const int pos = atomicAdd(&C.fill[g][0], 1);
-                if (pos < CAP) B0[pos] = v;
+                if (pos < CAP) {
+                    B0[pos] = v;
+                    I0[pos] = i;
+                }
             }
-            if ((unsigned)(b - bl1) <= (unsigned)bw1) {
+            if ((unsigned)(abs(2 * b - c2) - dl2) <= (unsigned)dw2) {
                 const int pos = atomicAdd(&C.fill[g][1], 1);
-                if (pos < CAP) B1[pos] = v;
+                if (pos < CAP) {
+                    B1[pos] = v;
+                    I1[pos] = i;
+                }
             }
         };
         for (int i = 4 * q.t; i < n4; i += 4 * GS) {
             const float4 y4 = y.get4(i);
-            gather(y4.x);
-            gather(y4.y);
-            gather(y4.z);
-            gather(y4.w);
+            gather(y4.x, i);
+            gather(y4.y, i + 1);
+            gather(y4.z, i + 2);
+            gather(y4.w, i + 3);
         }
-        for (int i = n4 + q.t; i < n; i += GS) gather(y.get(i));
+        for (int i = n4 + q.t; i < n; i += GS) gather(y.get(i), i);
         q.sync();
-        gpick(q, B0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2);
+        gpick(q, B0, I0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2, im1, im2);
         if (ap) {
             // #(y <= med) = #(y <= m1): keys below the run plus gathered keys <= m1
             int c = 0;
@@ -416,64 +547,92 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
             npos = n - nle;
             if (npos > 0) {
                 const int s3 = nle + (npos - 1) / 2 - c_lo1, s4 = nle + npos / 2 - c_lo1;
-                if (s3 < 0 || s4 >= cnt1) {
+                if (s3 < 0 || s4 >= cnt1)
                     fb = 2;   // the positive count differed from the guess
-                } else {
-                    if (q.t == 0) C.pv1[g] = C.pv2[g] = qnan;
-                    q.sync();
-                    gpick(q, B1, cnt1, s3, s4, C, p1, p2);
-                }
+                else
+                    gpick(q, B1, I1, cnt1, s3, s4, C, p1, p2, ip1, ip2);
             }
         } else {
-            // D_P: |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
-            float dmax = D.cov ? 4.0f * C.scale[g] : 0.0f;
-            const float hard =
-                __fmul_rn(__fadd_rn(D.rc, fabsf(m - C.lo_b[g] - 0.5f * (float)NB / sc)), 1.0001f);
-            if (!(dmax > 0.0f) || dmax > hard) dmax = hard;
-            if (!(dmax > 0.0f)) dmax = 1.0f;
-            const float scd = __fdiv_rn((float)NB, dmax);
-            for (int b = q.t; b < NB / 4; b += GS) reinterpret_cast<uint4*>(H)[b] = make_uint4(0u, 0u, 0u, 0u);
-            q.sync();
-            for (int i = 4 * q.t; i < n4; i += 4 * GS) {
-                const float4 y4 = y.get4(i);
-                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.x, m)), scd, 0.0f)], 1u);
-                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.y, m)), scd, 0.0f)], 1u);
-                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.z, m)), scd, 0.0f)], 1u);
-                atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.w, m)), scd, 0.0f)], 1u);
-            }
-            for (int i = n4 + q.t; i < n; i += GS) atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y.get(i), m)), scd, 0.0f)], 1u);
-            q.sync();
-            int da, dca, db, dcb;
-            gfind(q, H, k1, k2, C, da, dca, db, dcb);
-            const int cntd = dcb + (int)H[db] - dca;
-            if (cntd > CAP) {
-                fb = 2;
-            } else {
-                if (q.t == 0) {
-                    C.fill[g][1] = 0;
-                    C.pv1[g] = C.pv2[g] = qnan;
-                }
-                q.sync();
-                const int bwd = db - da;
-                auto gd = [&](float v) {
-                    const float dv = fabsf(__fsub_rn(v, m));
-                    const int b = bucket_fma(dv, scd, 0.0f);
-                    if ((unsigned)(b - da) <= (unsigned)bwd) {
-                        const int pos = atomicAdd(&C.fill[g][1], 1);
-                        if (pos < CAP) B1[pos] = dv;
+            bool ok = dl2 != OFF;
+            if (ok) {
+                // L keys lie below m1 <= m, R keys above m2 >= m; deviations in place, and the extremes of each run
+                float lmin = FLT_MAX, lmax = -FLT_MAX, rmin = FLT_MAX, rmax = -FLT_MAX;
+                for (int t = q.t; t < cnt1; t += GS) {
+                    const float v = B1[t];
+                    if (v < m) {
+                        lmin = fminf(lmin, v);
+                        lmax = fmaxf(lmax, v);
+                    } else {
+                        rmin = fminf(rmin, v);
+                        rmax = fmaxf(rmax, v);
                     }
-                };
+                    B1[t] = fabsf(__fsub_rn(v, m));
+                }
+                float la, lb, ra, rb;
+                gminmax(q, lmin, lmax, C, la, lb);
+                gminmax(q, rmin, rmax, C, ra, rb);
+                const int s1 = k1 - c_in, s2 = k2 - c_in;
+                ok = lb > -FLT_MAX && ra < FLT_MAX && s1 >= 0 && s2 < cnt1;
+                if (ok) {
+                    gpick(q, B1, I1, cnt1, s1, s2, C, p1, p2, ip1, ip2);
+                    // keys between the runs lie in (max L, min R), keys outside below min L or above max R
+                    const float inner = fmaxf(__fsub_rn(m, lb), __fsub_rn(ra, m));
+                    const float outer = fminf(__fsub_rn(m, la), __fsub_rn(rb, m));
+                    ok = inner <= p1 && outer >= p2;
+                }
+            }
+            if (!ok) {
+                // |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
+                float dmax = D.cov ? 4.0f * C.scale[g] : 0.0f;
+                const float hard =
+                    __fmul_rn(__fadd_rn(D.rc, fabsf(m - C.lo_b[g] - 0.5f * (float)NB / sc)), 1.0001f);
+                if (!(dmax > 0.0f) || dmax > hard) dmax = hard;
+                if (!(dmax > 0.0f)) dmax = 1.0f;
+                const float scd = __fdiv_rn((float)NB, dmax);
+                for (int b = q.t; b < NB / 4; b += GS) reinterpret_cast<uint4*>(H)[b] = make_uint4(0u, 0u, 0u, 0u);
+                q.sync();
                 for (int i = 4 * q.t; i < n4; i += 4 * GS) {
                     const float4 y4 = y.get4(i);
-                    gd(y4.x);
-                    gd(y4.y);
-                    gd(y4.z);
-                    gd(y4.w);
+                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.x, m)), scd, 0.0f)], 1u);
+                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.y, m)), scd, 0.0f)], 1u);
+                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.z, m)), scd, 0.0f)], 1u);
+                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.w, m)), scd, 0.0f)], 1u);
                 }
-                for (int i = n4 + q.t; i < n; i += GS) gd(y.get(i));
+                for (int i = n4 + q.t; i < n; i += GS)
+                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y.get(i), m)), scd, 0.0f)], 1u);
                 q.sync();
-                gpick(q, B1, cntd, k1 - dca, k2 - dca, C, p1, p2);
+                int da, dca, db, dcb;
+                gfind(q, H, k1, k2, C, da, dca, db, dcb);
+                const int cntd = dcb + (int)H[db] - dca;
+                if (cntd > CAP) {
+                    fb = 2;
+                } else {
+                    if (q.t == 0) C.fill[g][1] = 0;
+                    q.sync();
+                    const int bwd = db - da;
+                    auto gd = [&](float v, int i) {
+                        const float dv = fabsf(__fsub_rn(v, m));
+                        const int b = bucket_fma(dv, scd, 0.0f);
+                        if ((unsigned)(b - da) <= (unsigned)bwd) {
+                            const int pos = atomicAdd(&C.fill[g][1], 1);
+                            if (pos < CAP) {
+                                B1[pos] = dv;
+                                I1[pos] = i;
+                            }
+                        }
+                    };
+                    for (int i = 4 * q.t; i < n4; i += 4 * GS) {
+                        const float4 y4 = y.get4(i);
+                        gd(y4.x, i);
+                        gd(y4.y, i + 1);
+                        gd(y4.z, i + 2);
+                        gd(y4.w, i + 3);
+                    }
+                    for (int i = n4 + q.t; i < n; i += GS) gd(y.get(i), i);
+                    q.sync();
+                    gpick(q, B1, I1, cntd, k1 - dca, k2 - dca, C, p1, p2, ip1, ip2);
+                }
             }
         }
     }
@@ -488,36 +647,43 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
         }
         gminmax(q, kl, kh, C, kl, kh);
         unsigned* HF = H;
-        float* BF = B0;   // FB_CAP floats: B0 and B1
-        if (fb == 1) gselect(q, [&](int i) { return y.get(i); }, n, k1, k2, kl, kh, HF, BF, C, m1, m2, err);
+        float* BF = B0;   // FB_CAP values: B0 and B1
+        int* IF = I0;     // and their indices: I0 and I1
+        if (fb == 1)
+            gselect(q, [&](int i) { return y.get(i); }, n, k1, k2, kl, kh, HF, BF, IF, C, m1, m2, im1, im2, err);
         if (ap) {
             int c = 0;
             for (int i = q.t; i < n; i += GS) c += (y.get(i) <= m1);
             const int nle = gsum(q, c, C);
             npos = n - nle;
-            p1 = p2 = m1;
+            ip1 = ip2 = -1;
             if (npos > 0)
-                gselect(q, [&](int i) { return y.get(i); }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, HF, BF, C,
-                        p1, p2, err);
+                gselect(q, [&](int i) { return y.get(i); }, n, nle + (npos - 1) / 2, nle + npos / 2, kl, kh, HF, BF,
+                        IF, C, p1, p2, ip1, ip2, err);
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
             const float dmax = fmaxf(fabsf(__fsub_rn(kl, m)), fabsf(__fsub_rn(kh, m)));
-            gselect(q, [&](int i) { return fabsf(__fsub_rn(y.get(i), m)); }, n, k1, k2, 0.0f, dmax, HF, BF, C, p1, p2,
-                    err);
+            gselect(q, [&](int i) { return fabsf(__fsub_rn(y.get(i), m)); }, n, k1, k2, 0.0f, dmax, HF, BF, IF, C,
+                    p1, p2, ip1, ip2, err);
         }
     }
 
-    // ---- depth (FP64 on a handful of values) ----------------------------------------------
+    // ---- depth from FP64 projections of the selected points --------------------------------
+    const int sel = q.t == 0 ? im1 : (q.t == 1 ? im2 : (q.t == 2 ? ip1 : ip2));
+    if (q.t < 4) C.y64[g][q.t] = sel >= 0 ? proj64(D, u, sel) : 0.0;
+    q.sync();
     if (q.t == 0) {
-        const double med = ((double)m1 + (double)m2) * 0.5;
-        const double yzv = (double)C.yz[g];
-        double depth;
-        if (ap) {
-            const double madp = npos > 0 ? (((double)p1 - med) + ((double)p2 - med)) * 0.5 : 0.0;
-            depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
-        } else {
-            const double mad = ((double)p1 + (double)p2) * 0.5;
-            depth = depth_from(fabs(yzv - med), mad);
+        const double* Y = C.y64[g];
+        double depth = __longlong_as_double(0x7FF8000000000000LL);   // a failed selection (error flag set)
+        if (im1 >= 0 && im2 >= 0) {
+            const double med = (Y[0] + Y[1]) * 0.5;
+            if (ap) {
+                double madp = 0.0;
+                if (npos > 0) madp = ip1 >= 0 && ip2 >= 0 ? fmax(((Y[2] - med) + (Y[3] - med)) * 0.5, 0.0) : depth;
+                depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
+            } else if (ip1 >= 0 && ip2 >= 0) {
+                depth = depth_from(fabs(yzv - med), (fabs(Y[2] - med) + fabs(Y[3] - med)) * 0.5);
+            }
         }
         res[roff + g] = ResDev{depth, -1};
     }
@@ -528,8 +694,9 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
 // on keys recomputed from X.
 template <int G, int DP4, bool STREAM>
 __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const float* uS, unsigned* hist, float* buf,
-                                            int n, int npad, bool ap, const DsDev& D, int GA, int64_t roff,
-                                            ResDev* __restrict__ res, int* err, const float* kin)
+                                            int* ibuf, int n, int npad, bool ap, const DsDev& D, int GA,
+                                            const double* yz, int64_t roff, ResDev* __restrict__ res, int* err,
+                                            const float* kin)
 {
     constexpr int GS = cta_threads<G>() / G;   // threads per direction group
     const int tid = threadIdx.x;
@@ -538,15 +705,18 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
     if (g >= GA) return;   // inert direction (no CTA-wide barrier follows)
     unsigned* H = hist + g * NB;
     float* B0 = buf + (size_t)(2 * g) * CAP;   // two gather runs; FB_CAP = 2 * CAP for the fallback
+    int* I0 = ibuf + (size_t)(2 * g) * CAP;    // the point index of every gathered key
+    const float* u = uS + (size_t)g * D.ldx;
+    const double yzv = yz[roff + g];
     if (STREAM && kin) {
         const KeysArray y{kin + ((size_t)blockIdx.x * G + g) * npad};
-        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
     } else if (STREAM) {
-        const KeysRecomputed<DP4> y{D.X32, uS + (size_t)g * D.ldx, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
-        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+        const KeysRecomputed<DP4> y{D.X32, u, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
     } else {
         const KeysArray y{keys + (size_t)g * npad};
-        select_dir<GS>(q, y, C, H, B0, n, ap, D, roff, res, err);
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
     }
 }
 
@@ -558,7 +728,7 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
 template <int G, int DP4, bool STREAM>
 __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                 const float* __restrict__ z32, ResDev* __restrict__ res, int* err,
+                                                 const double* __restrict__ yz, ResDev* __restrict__ res, int* err,
                                                  const float* __restrict__ kin)
 {
     extern __shared__ __align__(16) float sm[];
@@ -574,6 +744,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     float* uS = keys + (STREAM ? (size_t)0 : (size_t)G * npad);   // G x ldx
     unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
     float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x 2 x CAP
+    int* ibuf = reinterpret_cast<int*>(buf + (size_t)G * 2 * CAP);       // G x 2 x CAP
 
     const int GA = T.nj;   // live directions; groups GA..G-1 are inert
     constexpr int NTK = cta_threads<G>();
@@ -589,13 +760,12 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
         const int g = tid >> 5, lane = tid & 31;
         const float* u = uS + g * ldx;
         float yc = 0.0f, qf = 0.0f;
-        for (int r = lane; r < d; r += 32) {
-            yc = fmaf(u[r], D.center[r], yc);
-            if (D.cov) {
-                const float* row = D.cov + (size_t)r * d;
-                float t = 0.0f;
-                for (int c2 = 0; c2 < d; ++c2) t = fmaf(row[c2], u[c2], t);
-                qf = fmaf(u[r], t, qf);
+        for (int r = lane; r < d; r += 32) yc = fmaf(u[r], D.center[r], yc);
+        if (D.cov) {
+            // lanes stride over the d x d entries, so the covariance loads are independent of each other
+            for (int e = lane; e < d * d; e += 32) {
+                const int r = e / d, c2 = e - r * d;
+                qf = fmaf(D.cov[e], __fmul_rn(u[r], u[c2]), qf);
             }
         }
 #pragma unroll
@@ -604,13 +774,6 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
             qf += __shfl_xor_sync(0xFFFFFFFFu, qf, o);
         }
         if (lane == 0) {
-            float a = 0.0f;
-            const float* zr = z32 + S.zoff32;
-            if (DP4 > 0) {
-                a = key_halves<(DP4 > 0 ? DP4 : 4)>(u, zr);   // y_z: same arithmetic as the keys
-            } else {
-                for (int l = 0; l < dp4; ++l) a = fmaf(u[l], zr[l], a);
-            }
             float half = D.rc * 1.0001f;
             if (D.cov) {
                 const float sg = sqrtf(fmaxf(qf, 0.0f));
@@ -620,7 +783,6 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 C.scale[g] = half;
             }
             if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
-            C.yz[g] = a;
             C.lo_b[g] = yc - half;
             C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
             C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
@@ -755,7 +917,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     }
     __syncthreads();
 
-    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, n, npad, ap, D, GA, S.roff + T.j0, res, err, kin);
+    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, ibuf, n, npad, ap, D, GA, yz, S.roff + T.j0, res, err, kin);
 }
 
 }  // namespace
@@ -764,7 +926,7 @@ size_t pdap_smem_bytes(int n, int group, int ldx, bool stream)
 {
     const size_t npad = stream ? 0 : ((size_t)n + 3) & ~(size_t)3;
     return sizeof(float) * ((size_t)group * npad + (size_t)group * ldx) + sizeof(unsigned) * (size_t)group * NB +
-           sizeof(float) * (size_t)group * 2 * CAP;
+           (sizeof(float) + sizeof(int)) * (size_t)group * 2 * CAP;
 }
 
 size_t pdap_smem_limit()
@@ -921,7 +1083,7 @@ __global__ void __launch_bounds__(KH_P) k_keys_halves(const TaskDev* __restrict_
 
 template <int G, int DP4, bool STREAM>
 static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots, const DsDev* ds,
-                            const float* U, const float* z32, ResDev* res, int* err, const float* kin, cudaStream_t st)
+                            const float* U, const double* yz, ResDev* res, int* err, const float* kin, cudaStream_t st)
 {
     cudaError_t e =
         cudaFuncSetAttribute(k_pdap2<G, DP4, STREAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -929,21 +1091,21 @@ static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<G, DP4, STREAM><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, z32, res, err, kin);
+    k_pdap2<G, DP4, STREAM><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, yz, res, err, kin);
     return cudaGetLastError();
 }
 
 template <int G, bool STREAM>
 static cudaError_t launch_g(int dp4, const TaskDev* tasks, int ntasks, size_t smem, const SlotDev* slots,
-                            const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, const float* kin,
+                            const DsDev* ds, const float* U, const double* yz, ResDev* res, int* err, const float* kin,
                             cudaStream_t st)
 {
     switch (dp4) {
-    case 4: return launch_t<G, 4, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 8: return launch_t<G, 8, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 12: return launch_t<G, 12, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 16: return launch_t<G, 16, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    default: return launch_t<G, 0, STREAM>(tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 4: return launch_t<G, 4, STREAM>(tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    case 8: return launch_t<G, 8, STREAM>(tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    case 12: return launch_t<G, 12, STREAM>(tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    case 16: return launch_t<G, 16, STREAM>(tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    default: return launch_t<G, 0, STREAM>(tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
     }
 }
 
@@ -954,7 +1116,7 @@ int pdap_dp4_class(int d)
 }
 
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
-                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
+                        const DsDev* ds, const float* U, const double* yz, ResDev* res, int* err, cudaStream_t st,
                         const float* kin)
 {
     if (ntasks <= 0) return cudaSuccess;
@@ -962,12 +1124,12 @@ cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group
     const int dp4 = variant & ~PDAP_STREAM;
     if (variant & PDAP_STREAM) {
         if (group != PDAP_STREAM_GROUP) return cudaErrorInvalidValue;
-        return launch_g<PDAP_STREAM_GROUP, true>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+        return launch_g<PDAP_STREAM_GROUP, true>(dp4, tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
     }
     switch (group) {
-    case 1: return launch_g<1, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 2: return launch_g<2, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
-    case 4: return launch_g<4, false>(dp4, tasks, ntasks, smem, slots, ds, U, z32, res, err, kin, st);
+    case 1: return launch_g<1, false>(dp4, tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    case 2: return launch_g<2, false>(dp4, tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
+    case 4: return launch_g<4, false>(dp4, tasks, ntasks, smem, slots, ds, U, yz, res, err, kin, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -458,7 +458,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
             if (P.pd_keys_ds[c] < 0) {
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
-                                     P.d_ds, P.U, P.z32, P.res, ctx->d_err, st));
+                                     P.d_ds, P.U, P.yz, P.res, ctx->d_err, st));
                 ctx->launches++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
                 continue;
@@ -474,7 +474,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
                 }
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
-                                     P.d_ds, P.U, P.z32, P.res, ctx->d_err, st, P.keys));
+                                     P.d_ds, P.U, P.yz, P.res, ctx->d_err, st, P.keys));
                 ctx->launches += 2;
                 ctx->stage_launches[RRS_STAGE_KEYS]++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
@@ -970,7 +970,7 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
                 if (!P.pd_tasks[c].empty())
                     CUDA_TRY(launch_pdap(P.d_pd[c], (int)P.pd_tasks[c].size(), P.pd_smem[c], P.pd_group[c],
                                          P.pd_variant[c], P.d_slots, P.d_ds, P.U,
-                                         P.z32, P.res, ctx->d_err, st));
+                                         P.yz, P.res, ctx->d_err, st));
         }
         ctx->launches += 4;
         trace("debug_round_depths: depth kernels enqueued");

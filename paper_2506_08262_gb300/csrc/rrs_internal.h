@@ -105,8 +105,9 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
                            int* err, cudaStream_t st);
 // group: directions per CTA (1, 2 or 4, from pdap_shape); variant: pdap_shape's kernel variant (the key
 // arithmetic class pdap_dp4_class(d), plus PDAP_STREAM), shared by every task
+// yz: the FP64 y_z = u'z of every direction (the direction generator's output), used for the depth
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
-                        const DsDev* ds, const float* U, const float* z32, ResDev* res, int* err, cudaStream_t st,
+                        const DsDev* ds, const float* U, const double* yz, ResDev* res, int* err, cudaStream_t st,
                         const float* kin = nullptr);
 // Keys of ntasks selection tasks (all of one dataset) into keys (pdap_keys_bytes), for
 // launch_pdap(..., kin = keys) on the same task range, with the selection kernel's own key arithmetic:

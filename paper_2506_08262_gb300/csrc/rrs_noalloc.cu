@@ -12,18 +12,21 @@
 // other allocating routine is called, on the device or on the host.
 //
 // The array lives in every device that loads the library until the process
-// exits.  Its device address is looked up once per device (on the first call
-// made with that device current) with cudaGetSymbolAddress; that first call
-// should therefore come before any stream capture.  All calls share the array
-// and it keeps the previous call's contents: the call clears what must start
-// at zero, and two calls whose work overlaps on the GPU (different streams,
-// or different host threads) race on it.  The call returns after its stream
-// has finished the work.
+// exits.  In host code its name is only a host-side stand-in, so every call
+// asks the runtime for its device address (cudaGetSymbolAddress, with the
+// calling device current) and hands that address to the kernels; asking on
+// every call keeps the address right even after a cudaDeviceReset.  The first
+// call on a device also loads the library's device code there, so that first
+// call should come before any stream capture.  All calls share the array and
+// it keeps the previous call's contents: the call clears what must start at
+// zero, and two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.  Every call waits for its stream twice
+// (to read the input check and the device-side error flags) and returns after
+// the stream has finished the work.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/rrs.h"
 #include "rrs_internal.h"
@@ -33,10 +36,6 @@ using namespace rrs;
 namespace {
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[RRS_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
 rrs_status noalloc_fail(rrs_status st, const char* fmt, ...)
 {
@@ -49,22 +48,16 @@ rrs_status noalloc_fail(rrs_status st, const char* fmt, ...)
     return st;
 }
 
-// Address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.
 rrs_status scratch_address(void** out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(RRS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(RRS_ERR_UNSUPPORTED, "device %d beyond table", dev);
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return noalloc_fail(RRS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return noalloc_fail(RRS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
     }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return RRS_OK;
 }
 
@@ -85,9 +78,13 @@ Layout layout(int64_t n, int ldx, int d, int64_t nq, int m, int gen_per, int hd_
 {
     Layout L{};
     size_t o = 0;
+    bool over = false;
+    // the caller bounds n, nq and nq * m by the scratch size first, so no product below wraps;
+    // take() marks the layout as too large once the running total passes the scratch size
     auto take = [&](size_t bytes) {
         const size_t at = o;
-        o = up256(o + (bytes ? bytes : 1));
+        if (bytes > (size_t)RRS_NOALLOC_SCRATCH_BYTES || o + bytes > (size_t)RRS_NOALLOC_SCRATCH_BYTES) over = true;
+        o = over ? o : up256(o + (bytes ? bytes : 1));
         return at;
     };
     L.ds = take(sizeof(DsDev));
@@ -106,7 +103,7 @@ Layout layout(int64_t n, int ldx, int d, int64_t nq, int m, int gen_per, int hd_
     L.yz = take(sizeof(double) * (size_t)nq * m);
     L.res = take(sizeof(ResDev) * (size_t)nq * m);
     L.err = take(sizeof(int) * 2);
-    L.total = o;
+    L.total = over ? (size_t)RRS_NOALLOC_SCRATCH_BYTES + 1 : o;
     return L;
 }
 
@@ -190,7 +187,15 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     if (!(cap_shrink > 0.0) || cap_shrink > 1.0) return noalloc_fail(RRS_ERR_INVALID_ARG, "cap_shrink not in (0, 1]");
     if (n_queries == 0) return RRS_OK;
     const int ldx = padded_stride(d);
-    const int m = (n_dirs + n_refinements - 1) / n_refinements;
+    const int m = (int)(((int64_t)n_dirs + n_refinements - 1) / n_refinements);
+    // n, n_queries and n_queries * m are at most the scratch size (2^25 bytes) and ldx is at most
+    // 1,028, so no size product of layout() can wrap a 64-bit size_t
+    const int64_t cap = (int64_t)RRS_NOALLOC_SCRATCH_BYTES;
+    if (n_queries > 0x7FFFFFFF || n_queries > cap || n > cap || (int64_t)n_queries * m > cap)
+        return noalloc_fail(RRS_ERR_BUDGET,
+                            "n = %lld, n_queries = %lld and n_dirs = %d need more than the %zu bytes of the "
+                            "static scratch of rrs_depth_noalloc",
+                            (long long)n, (long long)n_queries, n_dirs, (size_t)RRS_NOALLOC_SCRATCH_BYTES);
     if (kind == RRS_HALFSPACE && ldx > 440)
         return noalloc_fail(RRS_ERR_UNSUPPORTED, "d=%d too large for the FP32 halfspace kernel", d);
     int G = 0, pd_variant = 0;
@@ -215,14 +220,15 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
     const int hd_size = (m + hd_tasks - 1) / hd_tasks;
     const int hd_per = kind == RRS_HALFSPACE ? (m + hd_size - 1) / hd_size : 0;
     const int pd_per = kind == RRS_HALFSPACE ? 0 : (m + G - 1) / G;
+    if ((int64_t)n_queries * gen_per > 0x7FFFFFFF || (int64_t)n_queries * hd_per > 0x7FFFFFFF ||
+        (int64_t)n_queries * pd_per > 0x7FFFFFFF)
+        return noalloc_fail(RRS_ERR_UNSUPPORTED, "too many queries");
     const Layout L = layout(n, ldx, d, n_queries, m, gen_per, hd_per, pd_per);
     if (L.total > (size_t)RRS_NOALLOC_SCRATCH_BYTES)
         return noalloc_fail(RRS_ERR_BUDGET,
                             "this call needs %zu bytes of working memory; the static scratch of "
                             "rrs_depth_noalloc holds %zu bytes",
                             L.total, (size_t)RRS_NOALLOC_SCRATCH_BYTES);
-    if ((int64_t)n_queries * gen_per > 0x7FFFFFFF || n_queries > 0x7FFFFFFF)
-        return noalloc_fail(RRS_ERR_UNSUPPORTED, "too many queries");
 
     void* base = nullptr;
     rrs_status s = scratch_address(&base);
@@ -282,7 +288,7 @@ extern "C" rrs_status rrs_depth_noalloc(const void* X, int64_t n, int32_t d, int
         if (kind == RRS_HALFSPACE)
             NA_TRY(launch_hd_simt(hd, nq * hd_per, ldx, slots, ds, U, yz, z64, res, nullptr, err + 1, st));
         else
-            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, G, pd_variant, slots, ds, U, z32, res, err + 1, st));
+            NA_TRY(launch_pdap(pd, nq * pd_per, pd_smem, G, pd_variant, slots, ds, U, yz, res, err + 1, st));
         NA_TRY(launch_argmin(slots, arg, nq, U, res, cur, nxt, l, 0, st));
     }
     int flags = 0;

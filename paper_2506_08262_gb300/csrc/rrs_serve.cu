@@ -425,7 +425,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             const int cnt_all = (int)pd[key].size(), G = std::get<1>(key), krow = std::get<3>(key);
             if (krow < 0) {
                 S_TRY(launch_pdap(tl, cnt_all, pd_need[key], G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
-                                  S->d_z32, S->d_res, S->ctx->d_err, S->st));
+                                  S->d_yz, S->d_res, S->ctx->d_err, S->st));
                 continue;
             }
             // d > 16: keys by the tiled GEMM, then the selection on them, one scratch-sized chunk at a time
@@ -445,7 +445,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 S_TRY(launch_pdap_keys(tl + t0, cnt, G, S->d_slots, S->d_ds, S->ds_host[krow], S->d_U, S->d_keys,
                                        S->st));
                 S_TRY(launch_pdap(tl + t0, cnt, pd_need[key], G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
-                                  S->d_z32, S->d_res, S->ctx->d_err, S->st, S->d_keys));
+                                  S->d_yz, S->d_res, S->ctx->d_err, S->st, S->d_keys));
                 extra += 2;
             }
             extra--;   // counted once below

@@ -412,3 +412,86 @@ def test_rrs_rejects_bad_arguments():
         oracle.rrs(X, X, H, 5, 10, 0.5)       # k < r
     with pytest.raises(ValueError):
         oracle.rrs(X, X, H, 10, 2, 1.5)       # alpha > 1
+
+
+def _replay_depths(kind, X, z, U):
+    """Univariate depths of z along the rows of U, written out here (Sec. 2): exact halfspace counts from
+    rational arithmetic, projection / asymmetric projection depths from numpy FP64 medians."""
+    from fractions import Fraction
+    if kind == H:
+        Xf = [[Fraction(float(v)) for v in row] for row in X]
+        zf = [Fraction(float(v)) for v in z]
+        out = []
+        for u in U:
+            uf = [Fraction(float(v)) for v in u]
+            t = [sum(a * (b - c) for a, b, c in zip(uf, row, zf)) for row in Xf]
+            le = sum(1 for v in t if v <= 0)
+            ge = sum(1 for v in t if v >= 0)
+            out.append(min(le, ge))
+        return np.array(out, np.int64)
+    y = X.astype(np.float64) @ U.astype(np.float64).T
+    yz = U.astype(np.float64) @ z.astype(np.float64)
+    med = np.median(y, axis=0)
+    out = []
+    for j in range(U.shape[0]):
+        if kind == P:
+            spread = np.median(np.abs(y[:, j] - med[j]))
+            num = abs(yz[j] - med[j])
+        else:
+            pos = y[:, j][y[:, j] > med[j]] - med[j]
+            spread = np.median(pos) if pos.size else 0.0
+            num = max(yz[j] - med[j], 0.0)
+        out.append((1.0 if num == 0 else 0.0) if spread == 0 else 1.0 / (1.0 + num / spread))
+    return np.array(out)
+
+
+def _replay_rrs(kind, X, z, q, k, r, alpha, seed):
+    """Alg. 1 / Alg. S3 across rounds, written out here: round l draws its m directions about the current
+    pole, the round minimum is taken at its lowest index, and D_min, the best flat index l*m + j* and the
+    pole change only when the round minimum is strictly below D_min.  Returns (D_min, best, ties) where
+    ties counts later rounds whose minimum equalled the running D_min (a non-strict update would move the
+    best index there)."""
+    n, d = X.shape
+    m = -(-k // r)
+    pole = np.zeros(d, np.float32)
+    pole[0] = 1.0
+    run = n if kind == H else 1.0
+    best, ties = -1, 0
+    for l in range(r):
+        U = oracle.directions(seed, q, l, m, d, alpha, pole)
+        v = _replay_depths(kind, X, z, U)
+        ja = int(np.argmin(v))
+        if v[ja] < run:
+            run, best, pole = v[ja], l * m + ja, U[ja].copy()
+        elif v[ja] == run and best >= 0:
+            ties += 1
+    return run, best, ties
+
+
+def test_rrs_cross_round_update_is_strict():
+    # Small integer clouds: halfspace counts take few values, so later rounds often tie the running minimum;
+    # the oracle must keep the earlier best index and pole then (a <= update would move both).
+    rng = np.random.default_rng(31)
+    X = rng.integers(-5, 6, size=(12, 2)).astype(np.float64)
+    Z = np.vstack([X[3], X[7], rng.integers(-3, 4, size=(4, 2)).astype(np.float64)])
+    k, r, alpha, seed = 40, 5, 0.6, 5
+    out = oracle.rrs(X, Z, H, k, r, alpha, seed)
+    ties = 0
+    for q in range(Z.shape[0]):
+        run, best, t = _replay_rrs(H, X, Z[q], q, k, r, alpha, seed)
+        ties += t
+        assert out["count"][q] == run and out["best"][q] == best, q
+        assert out["depth"][q] == run / X.shape[0]
+    assert ties >= 3, "the case should exercise ties with the running minimum"
+
+
+@pytest.mark.parametrize("kind", [P, AP])
+def test_rrs_multi_round_replay_projection_depths(kind):
+    # r = 6 rounds with shrinking caps about the moving pole; depths and best flat indices from the replay
+    X, Z = workloads.gaussian_cloud(33 + kind, 257, 3, 6)
+    k, r, alpha, seed = 60, 6, 0.7, 8
+    out = oracle.rrs(X, Z, kind, k, r, alpha, seed)
+    for q in range(Z.shape[0]):
+        run, best, _ = _replay_rrs(kind, X, Z[q], q, k, r, alpha, seed)
+        np.testing.assert_allclose(out["depth"][q], run, rtol=1e-12)
+        assert out["best"][q] == best, q

@@ -48,6 +48,10 @@ def test_noalloc_matches_rrs_depth_two_calls_in_a_row(kind):
     X, Z = workloads.gaussian_cloud(40 + kind, 1537, 7, 23, dtype=np.float32)
     Xd, Zd = torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda()
     ref_d, ref_c = regular(Xd, Zd, kind, 150, 5, 0.6, 9)
+    # a different call first (another cloud, more queries, another seed and direction count), so the
+    # scratch holds unrelated contents when the compared calls run; then two compared calls in a row
+    X2, Z2 = workloads.gaussian_cloud(70 + kind, 2100, 7, 61, dtype=np.float32)
+    noalloc(torch.from_numpy(X2).cuda(), torch.from_numpy(Z2).cuda(), kind, 240, 6, 0.8, 4)
     for _ in range(2):
         got_d, got_c = noalloc(Xd, Zd, kind, 150, 5, 0.6, 9)
         if kind == rrs.RRS_HALFSPACE:
@@ -56,6 +60,28 @@ def test_noalloc_matches_rrs_depth_two_calls_in_a_row(kind):
         else:
             np.testing.assert_allclose(got_d, ref_d, rtol=1e-5, atol=0)
             assert np.all(got_c == -1)
+
+
+def test_noalloc_binding_refuses_bad_buffers():
+    # the C entry point takes raw device addresses; the binding refuses what would make the kernels
+    # read or write outside a buffer or through a host address
+    X = torch.zeros((50, 4), dtype=torch.float32, device="cuda")
+    Z = torch.zeros((3, 4), dtype=torch.float32, device="cuda")
+    ok_out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    cases = [
+        dict(X=X.cpu()),                                                  # host tensor
+        dict(Z=Z.double()),                                               # dtype differs from X's
+        dict(out=torch.zeros(3, dtype=torch.float32, device="cuda")),     # depth_out not float64
+        dict(out=torch.zeros(2, dtype=torch.float64, device="cuda")),     # depth_out too short
+        dict(cnt=torch.zeros(3, dtype=torch.int32, device="cuda")),       # count_out not int64
+        dict(X=torch.zeros((4, 50), dtype=torch.float32, device="cuda").t()),   # not contiguous
+        dict(X=np.zeros((50, 4), np.float32)),                            # numpy array
+    ]
+    for c in cases:
+        with pytest.raises(rrs.RRSError) as e:
+            rrs.rrs_depth_noalloc(c.get("X", X), 50, 4, rrs.RRS_F32, c.get("Z", Z), 3, rrs.RRS_PROJECTION, 20, 2,
+                                  0.5, 0, c.get("out", ok_out), c.get("cnt"))
+        assert e.value.status == rrs.RRS_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("kind", [rrs.RRS_PROJECTION, rrs.RRS_ASYM_PROJECTION])
