@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--grid-k", type=int, nargs="*", default=None, help="grid: only these direction counts (r = 1)")
     ap.add_argument("--rate", type=float, default=2000.0, help="c5: Poisson arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=3.0, help="c5: arrival window (s)")
+    ap.add_argument("--rates", type=float, nargs="*", default=None, help="c5 --sweep: arrival rates (requests/s)")
+    ap.add_argument("--work-limit", type=float, default=None,
+                    help="c5: the server's work limit per step (weighted point-direction pairs; 0 = none)")
     return ap.parse_args()
 
 
@@ -681,7 +684,8 @@ def _latency_stats(lat):
 def run_c5(args):
     """Poisson request stream through the continuous-batching server, against one rrs_depth call per
     request in arrival order.  Requests that would push the backlog of waiting queries beyond a bound are
-    shed (counted) in both arms."""
+    shed (counted) in both arms.  With --sweep both arms serve the stream at every rate of --rates (default:
+    1/8 .. 2x --rate)."""
     import collections
     import torch
     from __graft_entry__ import build
@@ -717,7 +721,9 @@ def run_c5(args):
     # ---- continuous batching ----------------------------------------------------------------
     def serve_stream(reqs):
         srv = rrs.rrs_server_create(ctx, max_slots, 100, 100, stream, precision=tc)
-        outs, lat, shed, served_q = {}, [], 0, 0
+        if args.work_limit is not None:
+            rrs.rrs_server_set_work_limit(srv, args.work_limit)
+        outs, lat, shed, served_q, steps = {}, [], 0, 0, 0
         inflight = collections.deque()
         backlog = 0
         t0 = time.perf_counter()
@@ -738,6 +744,7 @@ def run_c5(args):
                 i += 1
             if outs:
                 rrs.rrs_server_step(srv)
+                steps += 1
                 ev = torch.cuda.Event()
                 ev.record(stream)
                 inflight.append(ev)
@@ -756,31 +763,76 @@ def run_c5(args):
         rrs.rrs_server_destroy(srv)
         rrs.rrs_check(ctx, stream)
         return {"served_requests": len(lat), "shed_requests": shed, "queries": served_q,
-                "value": served_q / wall, "wall_s": wall, **_latency_stats(lat)}
+                "value": served_q / wall, "wall_s": wall, "steps": steps, **_latency_stats(lat)}
 
+    # ---- one rrs_depth call per request, arrival order ------------------------------------------
+    def per_request(reqs):
+        lat2, shed2, served2 = [], 0, 0
+        queue = collections.deque()
+        t0 = time.perf_counter()
+        i = 0
+        backlog = 0
+        while i < len(reqs) or queue:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i].t_arrival <= now:
+                nq = reqs[i].Z.shape[0]
+                if backlog + nq > backlog_limit:
+                    shed2 += 1
+                else:
+                    queue.append(i)
+                    backlog += nq
+                i += 1
+            if not queue:
+                time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)) if i < len(reqs) else 0)
+                continue
+            j = queue.popleft()
+            q = reqs[j]
+            nq = q.Z.shape[0]
+            out = np.empty(nq)
+            rrs.rrs_depth(ctx, ids[q.dataset], q.Z, nq, rrs.RRS_F32, False, q.kind, k, r, alpha, j,
+                          rrs.RRS_PREC_FP32_SIMT, out, None, None, None, False, stream)
+            lat2.append(time.perf_counter() - t0 - q.t_arrival)
+            backlog -= nq
+            served2 += nq
+        wall2 = time.perf_counter() - t0
+        return {"served_requests": len(lat2), "shed_requests": shed2, "queries": served2, "value": served2 / wall2,
+                "wall_s": wall2, **_latency_stats(lat2)}
+
+    limit_used = args.work_limit if args.work_limit is not None else "library default (RRS_SERVER_DEFAULT_WORK)"
     if args.sweep:
-        # rate sweep on the same resident datasets: the highest rate that sheds nothing and keeps p99
-        # below half the arrival window (the backlog does not grow over the window)
+        # both arms at every rate on the same resident datasets; a rate is stable when nothing is shed and
+        # the p99 stays below half the arrival window (the backlog does not grow over the window)
         sampler = ClockSampler(0)
         sampler.start()
         sweep = []
-        for f in (0.125, 0.25, 0.5, 1.0, 2.0):
-            rate = args.rate * f
+        rates = args.rates if args.rates else [args.rate * f for f in (0.125, 0.25, 0.5, 1.0, 2.0)]
+        for rate in rates:
             _, rq = workloads.c5(rate=rate, window_s=args.window, scale=args.scale)
             cb = serve_stream(rq)
-            sweep.append({"rate_req_per_s": rate, "offered_requests": len(rq), **cb})
+            pr = per_request(rq)
+            sweep.append({"rate_req_per_s": rate, "offered_requests": len(rq),
+                          "offered_queries": int(sum(x.Z.shape[0] for x in rq)),
+                          "continuous_batching": cb, "one_call_per_request_fp32": pr})
         clocks = sampler.stop()
-        stable = [x["rate_req_per_s"] for x in sweep
-                  if x["shed_requests"] == 0 and x.get("p99_ms", 1e30) <= 500.0 * args.window]
+
+        def stable(x):
+            return x["shed_requests"] == 0 and x.get("p99_ms", 1e30) <= 500.0 * args.window
         for did in ids:
             rrs.rrs_free(ctx, did)
         rrs.rrs_destroy(ctx)
-        line = {"metric": METRIC, "value": max(x["value"] for x in sweep), "unit": "query-depths/s", "n_gpus": 1,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16x3->f32 (halfspace), f32 (projection)", "data": "synthetic",
+        line = {"metric": METRIC, "value": max(x["continuous_batching"]["value"] for x in sweep),
+                "unit": "query-depths/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x3->f32 (halfspace), f32 (projection)", "data": "synthetic",
                 "config": {"workload": WORKLOAD_C5, "window_s": args.window, "scale": args.scale, "slots": max_slots,
-                           "backlog_limit_queries": backlog_limit, "rates": [x["rate_req_per_s"] for x in sweep]},
-                "sweep": sweep, "max_stable_rate_req_per_s": max(stable) if stable else None, "clocks": clocks}
+                           "backlog_limit_queries": backlog_limit, "work_limit": limit_used,
+                           "rates": [x["rate_req_per_s"] for x in sweep]},
+                "sweep": sweep,
+                "max_stable_rate_req_per_s": {
+                    "continuous_batching": max([x["rate_req_per_s"] for x in sweep
+                                                if stable(x["continuous_batching"])], default=None),
+                    "one_call_per_request_fp32": max([x["rate_req_per_s"] for x in sweep
+                                                      if stable(x["one_call_per_request_fp32"])], default=None)},
+                "clocks": clocks}
         print(json.dumps(line), flush=True)
         return
 
@@ -789,38 +841,7 @@ def run_c5(args):
     cb = serve_stream(reqs)
     clocks = sampler.stop()
     wall = cb["wall_s"]
-
-    # ---- one rrs_depth call per request, arrival order ------------------------------------------
-    lat2, shed2, served2 = [], 0, 0
-    queue = collections.deque()
-    t0 = time.perf_counter()
-    i = 0
-    backlog = 0
-    while i < len(reqs) or queue:
-        now = time.perf_counter() - t0
-        while i < len(reqs) and reqs[i].t_arrival <= now:
-            nq = reqs[i].Z.shape[0]
-            if backlog + nq > backlog_limit:
-                shed2 += 1
-            else:
-                queue.append(i)
-                backlog += nq
-            i += 1
-        if not queue:
-            time.sleep(max(0.0, min(0.001, reqs[i].t_arrival - now)) if i < len(reqs) else 0)
-            continue
-        j = queue.popleft()
-        q = reqs[j]
-        nq = q.Z.shape[0]
-        out = np.empty(nq)
-        rrs.rrs_depth(ctx, ids[q.dataset], q.Z, nq, rrs.RRS_F32, False, q.kind, k, r, alpha, j,
-                      rrs.RRS_PREC_FP32_SIMT, out, None, None, None, False, stream)
-        lat2.append(time.perf_counter() - t0 - q.t_arrival)
-        backlog -= nq
-        served2 += nq
-    wall2 = time.perf_counter() - t0
-    pr = {"served_requests": len(lat2), "shed_requests": shed2, "queries": served2, "value": served2 / wall2,
-          "wall_s": wall2, **_latency_stats(lat2)}
+    pr = per_request(reqs)
     for did in ids:
         rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
@@ -828,8 +849,9 @@ def run_c5(args):
             "ms_per_step": 1000 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3->f32 (halfspace), f32 (projection)", "data": "synthetic",
             "config": {"workload": WORKLOAD_C5, "rate_req_per_s": args.rate, "window_s": args.window,
-                       "requests_offered": len(reqs), "scale": args.scale, "slots": max_slots,
-                       "backlog_limit_queries": backlog_limit},
+                       "requests_offered": len(reqs), "queries_offered": int(sum(x.Z.shape[0] for x in reqs)),
+                       "scale": args.scale, "slots": max_slots, "backlog_limit_queries": backlog_limit,
+                       "work_limit": limit_used},
             "continuous_batching": cb, "one_call_per_request_fp32": pr, "clocks": clocks}
     print(json.dumps(line), flush=True)
 

@@ -174,20 +174,36 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
                              int32_t use_graph, void* stream);
 
 /*
- * rrs_autotune - pick the selection kernel's directions per CTA (1, 2 or 4)
- * for projection / asymmetric projection depth on this dataset with m =
- * ceil(n_dirs / n_refinements) directions per round: each feasible choice is
- * timed on one round of probe queries (rows of the dataset, two per SM) and the
- * fastest is cached in the context; later rrs_depth / rrs_depth_batched calls
- * with the same (n, d, m) use it.  Without tuning a shared-memory heuristic
- * decides.  Results never depend on the choice.  *choice_out (optional)
- * receives it (0 for halfspace depth, which has nothing to tune, and 0 when
- * no choice keeps the keys in shared memory: they then live in device memory
- * and the kernel runs with a fixed shape).
+ * rrs_autotune - pick the selection kernel for projection / asymmetric
+ * projection depth on this dataset with m = ceil(n_dirs / n_refinements)
+ * directions per round: 1, 2 or 4 directions per CTA with the keys held in
+ * shared memory, or RRS_SELECT_WARP (one warp per direction, keys re-formed
+ * from X at every pass; d <= 16 and n <= 12,288).  Each feasible choice is
+ * timed on one round of probe queries (rows of the dataset, two per SM) and
+ * the fastest is cached in the context; later rrs_depth / rrs_depth_batched
+ * calls with the same (n, d, m) use it.  Without tuning a shared-memory
+ * heuristic picks among the kernels that hold the keys.  Results
+ * never depend on the choice.  *choice_out (optional) receives it (0 for
+ * halfspace depth, which has nothing to tune, and 0 when no choice keeps the
+ * keys in shared memory: they then live in device memory and the kernel runs
+ * with a fixed shape).
  * Synchronous.  Errors: INVALID_ARG, NOT_FOUND, CUDA.
  */
+#define RRS_SELECT_WARP 64
 rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,
                         int32_t* choice_out);
+
+/*
+ * rrs_select_kernel - fix the selection kernel for (this dataset's n and d,
+ * m = ceil(n_dirs / n_refinements)) instead of timing it: choice 1, 2 or 4
+ * (directions per CTA, keys in shared memory), RRS_SELECT_WARP, or 0 to drop a
+ * fixed or tuned choice and return to the default.  A choice that does not
+ * fit the dataset falls back to the default at launch.  Results never depend
+ * on the choice.  Errors: INVALID_ARG (NULL context, unknown choice),
+ * NOT_FOUND.
+ */
+rrs_status rrs_select_kernel(rrs_ctx* ctx, int64_t dataset_id, int32_t n_dirs, int32_t n_refinements,
+                             int32_t choice);
 
 /* Text for a status code (static storage). */
 const char* rrs_status_string(rrs_status status);
@@ -279,9 +295,12 @@ rrs_status rrs_profile_read(rrs_ctx* ctx, double* ms_out, int64_t* launches_out)
  * on the device.  Requests queue in arrival order; each rrs_server_step admits
  * the waiting requests that fit in the free slots, runs ONE refinement round
  * (Alg. 4: generate, project + univariate depth, minimum and pole update) for
- * every active query in shared launches -- each query at its own round -- and
- * retires the requests whose last round just ran by copying their depths to the
- * caller's host buffer.  Requests that arrive while others are on the GPU thus
+ * a set of active queries in shared launches -- each query at its own round --
+ * and retires the requests whose queries have all run their last round by
+ * copying their depths to the caller's host buffer.  The set is bounded by the
+ * server's work limit (rrs_server_set_work_limit): every active request, oldest
+ * first, takes up to a quarter of the limit (at least one query), then the
+ * oldest requests fill the rest.  Requests that arrive while others are on the GPU thus
  * join the next step's launches.  Every query keeps its own direction stream
  * (counter q = its row in its request) and state, so a request's depths do not
  * depend on what else is being served: they equal rrs_depth's results on
@@ -315,14 +334,29 @@ rrs_status rrs_server_submit(rrs_server* server, int64_t dataset_id, const void*
                              double cap_shrink, uint64_t seed, double* depth_out, int64_t* request_id_out);
 
 /*
- * rrs_server_step - admit what fits, run one round for all active queries,
- * retire finished requests (their host copies are enqueued on the stream).
- * Returns after enqueueing.  *active_queries_out / *pending_requests_out
- * (optional) receive the queries in flight and the requests still waiting.
- * Each step is one refinement round (Alg. 4) for every active query, at that
- * query's own round.  Errors: INVALID_ARG (NULL server), CUDA.
+ * rrs_server_step - admit what fits, run one round for the queries the work
+ * limit lets in, retire finished requests (their host copies are enqueued on
+ * the stream).  Returns after enqueueing.  *active_queries_out /
+ * *pending_requests_out (optional) receive the admitted queries and the
+ * requests still waiting.  Each step is one refinement round (Alg. 4) for each
+ * chosen query, at that query's own round.  Errors: INVALID_ARG (NULL server),
+ * CUDA.
  */
 rrs_status rrs_server_step(rrs_server* server, int32_t* active_queries_out, int32_t* pending_requests_out);
+
+/*
+ * rrs_server_set_work_limit - bound one step's work: the weighted number of
+ * point-direction pairs (n x m per query and round; halfspace pairs on the
+ * tensor cores weigh 0.1, all others 1) of the queries that run a round in
+ * one step.  A step always runs at least one query, so no request starves.
+ * 0 runs every admitted query at every step (the GPU work of a step then grows
+ * with the admitted backlog, and so does every request's latency).  The
+ * default, RRS_SERVER_DEFAULT_WORK, keeps a step at roughly ten milliseconds
+ * of selection work on a GB300.  Errors: INVALID_ARG (NULL server, negative or
+ * non-finite limit).
+ */
+#define RRS_SERVER_DEFAULT_WORK 4e9
+rrs_status rrs_server_set_work_limit(rrs_server* server, double max_pairs_per_step);
 
 /* rrs_server_poll - *done_out = 1 once the request's depths are in its host
  * buffer (the request is then forgotten), else 0.  Errors: NOT_FOUND, CUDA. */

@@ -35,6 +35,7 @@ RRS_ERR_UNSUPPORTED = -7
 RRS_F32, RRS_F64 = 0, 1
 RRS_HALFSPACE, RRS_PROJECTION, RRS_ASYM_PROJECTION = 0, 1, 2
 RRS_PREC_FP32_SIMT, RRS_PREC_SPLIT_BF16X3 = 0, 1
+RRS_SELECT_WARP = 64
 
 
 class RRSError(RuntimeError):
@@ -88,6 +89,8 @@ _SIGS = {
     "rrs_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_autotune": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                       ctypes.c_void_p], ctypes.c_int32),
+    "rrs_select_kernel": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+                          ctypes.c_int32),
     "rrs_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
@@ -99,6 +102,7 @@ _SIGS = {
                            ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_server_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int32),
     "rrs_server_poll": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int32),
+    "rrs_server_set_work_limit": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int32),
     "rrs_server_destroy": ([ctypes.c_void_p], ctypes.c_int32),
     "rrs_depth_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
@@ -277,6 +281,10 @@ def rrs_server_step(server: int):
     return a.value, p.value
 
 
+def rrs_server_set_work_limit(server: int, max_pairs_per_step: float) -> None:
+    _check(load().rrs_server_set_work_limit(server, float(max_pairs_per_step)), "rrs_server_set_work_limit")
+
+
 def rrs_server_poll(server: int, request_id: int) -> bool:
     done = ctypes.c_int32()
     _check(load().rrs_server_poll(server, request_id, ctypes.byref(done)), "rrs_server_poll")
@@ -296,6 +304,11 @@ def rrs_autotune(ctx: int, dataset_id: int, kind: int, n_dirs: int, n_refinement
     choice = ctypes.c_int32()
     _check(load().rrs_autotune(ctx, dataset_id, kind, n_dirs, n_refinements, ctypes.byref(choice)), "rrs_autotune")
     return choice.value
+
+
+def rrs_select_kernel(ctx: int, dataset_id: int, n_dirs: int, n_refinements: int, choice: int) -> None:
+    """Fix the selection kernel (1, 2, 4 directions per CTA, RRS_SELECT_WARP, or 0 for the default)."""
+    _check(load().rrs_select_kernel(ctx, dataset_id, n_dirs, n_refinements, choice), "rrs_select_kernel")
 
 
 def rrs_check(ctx: int, stream=None) -> None:

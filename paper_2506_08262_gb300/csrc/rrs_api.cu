@@ -1044,8 +1044,10 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     CUDA_TRY(cudaEventCreate(&b));
     int best = 0;
     float best_ms = 0.0f;
-    for (int G : {1, 2, 4}) {
-        if (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit()) continue;
+    for (int G : {1, 2, 4, PDAP_WARP_GROUP}) {
+        if (G == PDAP_WARP_GROUP ? !pdapw_eligible(D.n, D.d)
+                                 : (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit()))
+            continue;
         ReqView R{};
         R.dset = &D;
         R.Z = zd;
@@ -1082,6 +1084,25 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     if (best) ctx->pd_tune[key] = best;
     if (choice_out) *choice_out = best;
     return check_device_errors(ctx, 0);
+}
+
+rrs_status rrs_select_kernel(rrs_ctx* ctx, int64_t dataset_id, int32_t n_dirs, int32_t n_refinements, int32_t choice)
+{
+    if (!ctx) return fail(RRS_ERR_INVALID_ARG, "NULL context");
+    if (choice != 0 && choice != 1 && choice != 2 && choice != 4 && choice != PDAP_WARP_GROUP)
+        return fail(RRS_ERR_INVALID_ARG, "unknown selection kernel choice %d", choice);
+    if (n_refinements < 1 || n_dirs < n_refinements) return fail(RRS_ERR_INVALID_ARG, "need n_dirs >= n_refinements >= 1");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->datasets.find(dataset_id);
+    if (it == ctx->datasets.end()) return fail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)dataset_id);
+    const Dataset& D = it->second;
+    const int m = (int)(((int64_t)n_dirs + n_refinements - 1) / n_refinements);
+    const auto key = std::make_tuple(D.n, D.ldx, m);
+    if (choice == 0)
+        ctx->pd_tune.erase(key);
+    else
+        ctx->pd_tune[key] = choice;
+    return RRS_OK;
 }
 
 rrs_status rrs_check(rrs_ctx* ctx, void* stream)

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/rrs.h"
+
 namespace rrs {
 
 // A resident dataset, as the kernels see it.
@@ -150,9 +152,18 @@ constexpr int PDAP_STREAM = 0x100;
 // Largest n the selection kernels take: point indices and the padded key count (n rounded up to 4) are int.
 constexpr int64_t PDAP_MAX_N = 0x7FFFFFC0;
 constexpr int PDAP_STREAM_GROUP = 2;
+// Selection-kernel variant bit: one warp per direction, up to PDAPW_DIRS directions per CTA, keys re-formed
+// from X at every pass (d <= 16, n <= PDAPW_MAX_N: 16-bit bucket counters); the low byte holds d.  Asking
+// pdap_shape for group PDAP_WARP_GROUP selects it where it applies.
+constexpr int PDAP_WARP = 0x200;
+constexpr int PDAPW_DIRS = 12;
+constexpr int64_t PDAPW_MAX_N = 12288;
+constexpr int PDAP_WARP_GROUP = RRS_SELECT_WARP;
+size_t pdapw_smem_bytes(int d);
+bool pdapw_eligible(int64_t n, int d);
 struct PdapShape {
     int group;        // directions per CTA
-    int variant;      // pdap_dp4_class(d), plus PDAP_STREAM
+    int variant;      // pdap_dp4_class(d), plus PDAP_STREAM; or PDAP_WARP | d
     size_t smem;      // dynamic shared memory per CTA
     bool keys_gemm;   // keys formed first by launch_pdap_keys
 };

@@ -3,12 +3,18 @@
 // A server owns a fixed pool of query slots on the device.  Requests wait in a
 // FIFO until enough slots are free; every rrs_server_step admits what fits,
 // then runs ONE refinement round (Alg. 4: generate, project + univariate depth,
-// minimum and pole update) for every active slot in shared launches -- each
-// slot at its own round -- and retires the requests whose last round just ran,
-// copying their depths to the caller's host buffer.  A request therefore joins
-// the GPU work of requests already in flight at the next step, and its
-// results do not depend on what else is in the mix: every query keeps its own
-// direction stream (counter index = row within its request) and state.
+// minimum and pole update) for a set of admitted queries in shared launches --
+// each query (slot) at its own round -- and retires the requests whose queries
+// have all run their last round, copying their depths to the caller's host
+// buffer.  The set is bounded by a work limit (weighted point-direction pairs
+// per step): every admitted request, oldest first, may take up to a quarter of
+// the limit (at least one query), then the oldest requests fill the rest.  So
+// a step's duration stays bounded however much is admitted, small requests
+// progress beside large ones, and a large request runs its queries in pieces
+// at full occupancy.  A request joins the GPU work of requests already in
+// flight at the next step, and its results do not depend on what else is in
+// the mix: every query keeps its own direction stream (counter index = row
+// within its request) and state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,7 +67,9 @@ struct Request {
     void* zdev = nullptr;
     double* ddev = nullptr;
     std::vector<int32_t> slots;
-    int rounds_done = 0;
+    std::vector<int32_t> sround;   // rounds run by each of its slots
+    int64_t rounds_left = 0;       // sum over its slots of the rounds still to run
+    double slot_work = 0.0;        // weighted point-direction pairs of one round of one query
     cudaEvent_t done = nullptr;
     bool finished = false;
 };
@@ -123,6 +131,7 @@ struct rrs_server {
     std::vector<DsDev> ds_host;
     int64_t next_id = 1;
     int active_queries = 0;
+    double work_limit = RRS_SERVER_DEFAULT_WORK;   // weighted pairs per step (0: every admitted query)
 };
 
 namespace {
@@ -196,6 +205,12 @@ rrs_status admit(rrs_server* S)
         S_TRY(cudaMallocAsync(&R->zdev, zbytes, S->st));
         S_TRY(cudaMallocAsync((void**)&R->ddev, sizeof(double) * R->nq, S->st));
         S_TRY(cudaMemcpyAsync(R->zdev, R->Zhost, zbytes, cudaMemcpyHostToDevice, S->st));
+        // cost weight of a pair: the tensor-core halfspace path runs about ten times as many pairs per second
+        // as the FP32 and selection paths (measured)
+        const bool tc = R->kind == RRS_HALFSPACE && S->precision == RRS_PREC_SPLIT_BF16X3 && D.kp > 0;
+        R->slot_work = (double)D.n * R->m * (tc ? 0.1 : 1.0);
+        R->sround.assign((size_t)R->nq, 0);
+        R->rounds_left = R->nq * (int64_t)R->r;
         for (int64_t q = 0; q < R->nq; ++q) {
             const int32_t slot = S->free_slots.back();
             S->free_slots.pop_back();
@@ -344,6 +359,37 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
     rrs_status s = admit(S);
     if (s != RRS_OK) return s;
     if (!S->active.empty()) {
+        // queries of this step: every request, oldest first, up to a quarter of the work limit (at least one
+        // query); then the oldest requests fill the rest.  pick[i] lists slot positions of active[i].
+        const size_t na = S->active.size();
+        std::vector<std::vector<int32_t>> pick(na);
+        std::vector<size_t> cursor(na, 0);   // next slot position to consider
+        const bool capped = S->work_limit > 0.0;
+        double used = 0.0;
+        auto take = [&](size_t i, double share) {
+            Request* R = S->active[i];
+            double mine = 0.0;
+            while (cursor[i] < R->slots.size()) {
+                const size_t p = cursor[i];
+                if (R->sround[p] >= R->r) {
+                    ++cursor[i];
+                    continue;
+                }
+                const bool first = pick[i].empty() && (used == 0.0 || share < 1.0);
+                if (capped && !first && (mine + R->slot_work > share * S->work_limit ||
+                                         used + R->slot_work > S->work_limit))
+                    break;
+                pick[i].push_back((int32_t)p);
+                mine += R->slot_work;
+                used += R->slot_work;
+                ++cursor[i];
+            }
+        };
+        for (size_t i = 0; i < na; ++i) {
+            if (capped && used >= S->work_limit) break;
+            take(i, 0.25);
+        }
+        for (size_t i = 0; i < na && capped && used < S->work_limit; ++i) take(i, 1.0);
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
         std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
@@ -353,7 +399,9 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         std::map<std::tuple<size_t, int, int, int>, size_t> pd_need;
         std::vector<int32_t> arg;
         const size_t classes[] = {24 * 1024, 48 * 1024, 72 * 1024, 110 * 1024, pdap_smem_limit()};
-        for (Request* R : S->active) {
+        for (size_t ai = 0; ai < na; ++ai) {
+            Request* R = S->active[ai];
+            if (pick[ai].empty()) continue;
             const DsDev& D = S->ds_host[S->ds_index[R->dataset]];
             PdapShape sh{};
             size_t cls = 0;
@@ -369,7 +417,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
             const int hper = (R->m + ((R->m + 63) / 64) - 1) / ((R->m + 63) / 64);
             const int row = S->ds_index[R->dataset];
             const bool use_tc = R->kind == RRS_HALFSPACE && S->precision == RRS_PREC_SPLIT_BF16X3 && D.kp > 0;
-            for (int32_t slot : R->slots) {
+            for (int32_t pos : pick[ai]) {
+                const int32_t slot = R->slots[pos];
                 for (int j0 = 0; j0 < R->m; j0 += 128) gen.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
                 if (use_tc) {
                     // slots of a request need not be adjacent: one task never crosses a slot
@@ -455,9 +504,12 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         S->ctx->launches += 3 + pd.size() + tc.size() + extra;
         // retire requests whose last round just ran
         std::vector<Request*> still;
+        for (size_t ai = 0; ai < na; ++ai) {
+            for (int32_t pos : pick[ai]) S->active[ai]->sround[pos]++;
+            S->active[ai]->rounds_left -= (int64_t)pick[ai].size();
+        }
         for (Request* R : S->active) {
-            R->rounds_done++;
-            if (R->rounds_done == R->r) {
+            if (R->rounds_left == 0) {
                 S_TRY(cudaMemcpyAsync(R->out_host, R->ddev, sizeof(double) * R->nq, cudaMemcpyDeviceToHost, S->st));
                 S_TRY(cudaEventCreateWithFlags(&R->done, cudaEventDisableTiming));
                 S_TRY(cudaEventRecord(R->done, S->st));
@@ -476,6 +528,15 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
     }
     if (active_queries_out) *active_queries_out = S->active_queries;
     if (pending_requests_out) *pending_requests_out = (int32_t)S->pending.size();
+    return RRS_OK;
+}
+
+rrs_status rrs_server_set_work_limit(rrs_server* S, double max_pairs_per_step)
+{
+    if (!S || !(max_pairs_per_step >= 0.0) || !(max_pairs_per_step <= 1e300))
+        return sfail(RRS_ERR_INVALID_ARG, "bad work limit");
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    S->work_limit = max_pairs_per_step;
     return RRS_OK;
 }
 
