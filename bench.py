@@ -49,14 +49,36 @@ WORKLOAD = ("projection + asymmetric projection depth, d=10, n=10000 (95% N(0,I)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant kernel, from a
-# single-pass ncu capture of the same launch shape on a GB300; reported only for that shape.
-TRAFFIC_PDAP_C2 = 3.60e6     # k_pdap2<2,12>, 50,000 directions x 10,000 points, d = 10
-TRAFFIC_HD_TC_C3 = 287.7e6   # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50
-# warp instructions the selection kernel executes per (point, direction) element at d = 10, n = 10,000
-# (ncu smsp__inst_executed.sum over one launch / its elements): the work actually done, every pass counted
-WARP_INSTR_PER_ELEMENT_PDAP_C2 = 1.92
+# Counters of the dominant kernels from ncu captures of the same launch shapes on a GB300 (profiles/ gives
+# the commands): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, and for the selection
+# kernel its executed warp instructions (smsp__inst_executed.sum) per (point, direction) element.  Each is
+# valid only for the kernel source it was taken from: `src_sha16` is the SHA-256 prefix of those files at
+# capture time, and a mismatch (the kernel changed since) reports null.
+CAPTURED = {
+    "k_pdap2_c2": {"src": ("paper_2506_08262_gb300/csrc/pdap.cu", "paper_2506_08262_gb300/csrc/rrs_internal.h"),
+                   "src_sha16": None, "traffic": None, "warp_instr_per_element": None},
+    "k_hd_tc_c3": {"src": ("paper_2506_08262_gb300/csrc/hd_tc.cu", "paper_2506_08262_gb300/csrc/async_sync.cuh",
+                           "paper_2506_08262_gb300/csrc/rrs_device.cuh"),
+                   "src_sha16": None, "traffic": None},
+}
 ISSUE_PER_SM_PER_CLK = 4     # one warp instruction per clock on each of the four SM sub-partitions
+
+
+def src_sha16(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured(key: str, field: str):
+    """A captured counter, or None when it was never taken or the kernel source changed since."""
+    c = CAPTURED[key]
+    if c.get(field) is None or c["src_sha16"] is None or c["src_sha16"] != src_sha16(c["src"]):
+        return None
+    return c[field]
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -67,6 +89,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="--impl reference: time the oracle on every query of the workload per step")
     ap.add_argument("--no-autotune", action="store_true",
                     help="headline: keep the shared-memory heuristic for the selection kernel's directions per CTA")
     ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
@@ -200,12 +224,36 @@ def oracle_sample_rate(per_kind: int):
 
 
 def run_reference(args):
+    """The reference arm: the CPU FP64 oracle, as it stands, on the host cores.  Default: a bounded sample
+    of the projection-depth workload per step.  --cpu-full: every query of that workload (1,000 of each
+    kind) per step.  --workload c3: the d = 50 halfspace workload on its first --nq queries (default 8)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    per_kind = max(1, oracle.max_threads())
+    if args.workload == "c3":
+        P = workloads.c3(nq=args.nq or 8)
+        threads = oracle.max_threads()
+        times = []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.rrs(P.X, P.Z, workloads.HALFSPACE, P.k, P.r, P.alpha, P.seed, nthreads=threads)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        value = P.Z.shape[0] * len(times) / sum(times)
+        sample = (f"{P.Z.shape[0]} queries of the d=50 halfspace workload (full n, k, r), OpenMP over queries on "
+                  f"{threads} host threads")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "query-depths/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD_C3, "step": sample},
+                "cpu_baseline": {"value": value, "unit": "query-depths/s", "cores": threads, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "query-depths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    per_kind = 1000 if args.cpu_full else max(1, oracle.max_threads())
     for _ in range(args.warmup):
         oracle_sample_rate(per_kind)
     times = []
@@ -219,7 +267,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "step": f"{per_kind} queries per kind (bounded sample)"},
+        "config": {"workload": WORKLOAD, "step": f"{per_kind} queries per kind" +
+                   (" (the whole workload)" if args.cpu_full else " (bounded sample)")},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                          "sample": r["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -241,12 +290,14 @@ def alu_ops_per_element(kind: int, d: int) -> int:
 
 def executed_work(captured_shape: bool, elements_per_launch: float, avg_launch_ms: float):
     """The selection kernel's executed instructions (all passes: projection, histograms, gathers, exact
-    ranks) against the SM issue peak, for the launch shape whose instruction count was measured."""
-    if not captured_shape:
+    ranks) against the SM issue peak, for the launch shape whose instruction count was measured on the
+    current kernel source (else None)."""
+    wipe = captured("k_pdap2_c2", "warp_instr_per_element")
+    if not captured_shape or wipe is None:
         return None
-    instr_per_s = elements_per_launch * WARP_INSTR_PER_ELEMENT_PDAP_C2 / (avg_launch_ms / 1000)
+    instr_per_s = elements_per_launch * wipe / (avg_launch_ms / 1000)
     peak = SM_COUNT * ISSUE_PER_SM_PER_CLK * SM_MAX_MHZ_NOMINAL * 1e6
-    return {"warp_instr_per_element": WARP_INSTR_PER_ELEMENT_PDAP_C2, "achieved_warp_instr_per_s": instr_per_s,
+    return {"warp_instr_per_element": wipe, "achieved_warp_instr_per_s": instr_per_s,
             "peak_warp_instr_per_s": peak, "frac": instr_per_s / peak,
             "source": "instructions per element from ncu smsp__inst_executed.sum; issue peak 152 SMs x 4 x 2070 MHz"}
 
@@ -304,7 +355,6 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = rrs.rrs_launch_count(ctx)
-    rrs.rrs_profile_enable(ctx, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
     for i in range(args.steps):
@@ -316,12 +366,20 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
-    prof = rrs.rrs_profile_read(ctx)
-    rrs.rrs_profile_enable(ctx, False)
     launches = rrs.rrs_launch_count(ctx) - launches0
     rrs.rrs_check(ctx, stream)
-    clocks = sampler.stop()
     step_ms = aggregate_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)) / args.steps, dev)
+    # per-kernel device times from a second pass over the same K steps with the library's per-launch CUDA
+    # events (recorded on the launching stream); the headline above ran without them
+    rrs.rrs_profile_enable(ctx, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = rrs.rrs_profile_read(ctx)
+    rrs.rrs_profile_enable(ctx, False)
+    rrs.rrs_check(ctx, stream)
+    clocks = sampler.stop()
 
     # end to end through the public API: pinned host query buffer in, host depths out
     Zh = torch.from_numpy(Z).pin_memory()
@@ -377,21 +435,24 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(Zh.numel() * 4 * len(kinds)),
                 "d2h_bytes_per_step": int(nq * 8 * len(kinds))},
         "roofline": {"bound": "alu", "kernel": "k_pdap", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_PDAP_C2 if args.nq == 0 else None,
+                     "frac": achieved / peak, "traffic": captured("k_pdap2_c2", "traffic") if args.nq == 0 else None,
                      "peak_source": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz (recipe unit counts and max clock)",
                      "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_launch_ms,
                      "executed": executed_work(args.nq == 0, nq * r * m * n * len(kinds) / launches_per_step,
                                                avg_launch_ms)},
         "stage_ms_per_step": {k2: v[0] / args.steps for k2, v in prof.items() if v[1]},
         "stage_share": stage_share,
+        "kernel_timing": "stage and kernel times from a second pass over the same K steps with per-launch CUDA "
+                         "events on the launching stream; the headline value from a pass without them",
         "clocks": clocks,
         "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and not args.no_halfspace:
-        # secondary: the tensor-core halfspace path against the FP32 path (d=50 workload, 1,000 queries)
-        line["halfspace_d50"] = measure_halfspace(1000, 2, 3)
+        # secondary: the tensor-core halfspace path on the full d=50 workload (10,000 queries) against the
+        # FP32 path on its first 1,000 queries
+        line["halfspace_d50"] = measure_halfspace(10_000, 2, 3, nq_fp32=1000)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample_rate(max(1, os.cpu_count() or 1))
+        cb = oracle_sample_rate(5 * max(1, os.cpu_count() or 1))
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                                 "sample": cb["sample"]}
     rrs.rrs_free(ctx, did)
@@ -407,9 +468,11 @@ WORKLOAD_C3 = ("halfspace depth, d=50, n=100000 Student-t(3) rows mapped by a ra
                "10000 queries from the same law, k=2000 dirs over r=20 rounds, alpha=0.9, FP32 data")
 
 
-def measure_halfspace(nq: int, steps: int, warmup: int):
-    """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path on `nq`
-    queries of the d=50 workload (full n, k, r).  Returns a dict with both arms and the speedup."""
+def measure_halfspace(nq: int, steps: int, warmup: int, nq_fp32: int = 0):
+    """Halfspace depth at d=50: split-BF16x3 tensor-core path on `nq` queries of the d=50 workload (full n,
+    k, r) against the FP32 CUDA-core path on the first `nq_fp32` of them (default all).  A query's result does
+    not depend on the batch, so the counts are compared on the common queries.  Returns a dict with both
+    arms and the speedup in query-depths per second."""
     import torch
     import paper_2506_08262_gb300 as rrs
     dev = torch.device("cuda", 0)
@@ -428,12 +491,14 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
         pass
     bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     out, results = {}, {}
+    nq_arm = {"tc": nq, "fp32": nq_fp32 or nq}
     for name, prec in (("tc", rrs.RRS_PREC_SPLIT_BF16X3), ("fp32", rrs.RRS_PREC_FP32_SIMT)):
-        dep = torch.empty(nq, dtype=torch.float64, device=dev)
-        cnt = torch.empty(nq, dtype=torch.int64, device=dev)
+        na = nq_arm[name]
+        dep = torch.empty(na, dtype=torch.float64, device=dev)
+        cnt = torch.empty(na, dtype=torch.int64, device=dev)
 
         def step():
-            rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F32, True, rrs.RRS_HALFSPACE, k, r, P.alpha, P.seed, prec,
+            rrs.rrs_depth(ctx, did, Zd, na, rrs.RRS_F32, True, rrs.RRS_HALFSPACE, k, r, P.alpha, P.seed, prec,
                           dep, cnt, None, None, True, stream)
         for _ in range(max(3, warmup)):
             step()
@@ -458,17 +523,17 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
         ms = sum(a.elapsed_time(b) for a, b in evs) / steps
         stage = "hd_tc" if prec == rrs.RRS_PREC_SPLIT_BF16X3 else "hd_simt"
         kms, kl = prof[stage]
-        elems_per_launch = nq * m * n
+        elems_per_launch = na * m * n
         avg_ms = kms / max(1, kl)
-        entry = {"ms_per_step": ms, "value": nq / (ms / 1000), "unit": "query-depths/s",
-                 "pd_per_s": nq * r * m * n / (ms / 1000), "kernel_ms_per_launch": avg_ms,
+        entry = {"queries": na, "ms_per_step": ms, "value": na / (ms / 1000), "unit": "query-depths/s",
+                 "pd_per_s": na * r * m * n / (ms / 1000), "kernel_ms_per_launch": avg_ms,
                  "kernel_share": kms / max(1e-9, sum(v[0] for v in prof.values())), "clocks": clocks}
         if name == "tc":
             flops = 6.0 * d * elems_per_launch   # three BF16 products of d terms per point-direction pair
             achieved = flops / (avg_ms / 1000) / 1e12
             entry["roofline"] = {"bound": "tensor", "kernel": "k_hd_tc", "achieved": achieved, "peak": bf16_peak,
                                  "unit": "TFLOP/s", "frac": achieved / bf16_peak,
-                                 "traffic": TRAFFIC_HD_TC_C3 if nq == 10_000 else None,
+                                 "traffic": captured("k_hd_tc_c3", "traffic") if nq == 10_000 else None,
                                  "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
                                  "flops_per_launch": flops}
         else:
@@ -480,7 +545,8 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
                                  "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 x 2070 MHz"}
         results[name] = cnt.cpu().numpy()
         out[name] = entry
-    same = bool(np.array_equal(results["tc"], results["fp32"]))
+    common = min(nq_arm.values())
+    same = bool(np.array_equal(results["tc"][:common], results["fp32"][:common]))
     # near-tie re-check rate of the tensor-core epilogue: the round-1 directions of a sample of queries,
     # counted by the debug entry point (points whose fast sign was not trusted / all point-direction pairs)
     ns = min(nq, 16)
@@ -497,15 +563,15 @@ def measure_halfspace(nq: int, steps: int, warmup: int):
     rrs.rrs_free(ctx, did)
     rrs.rrs_destroy(ctx)
     return {"workload": WORKLOAD_C3, "queries": nq, "n": n, "d": d, "k": k, "r": r, "tensor_core": out["tc"],
-            "fp32_cuda_core": out["fp32"], "speedup_tc_over_fp32": out["fp32"]["ms_per_step"] / out["tc"]["ms_per_step"],
-            "counts_identical": same, "tensor_core_recheck": recheck}
+            "fp32_cuda_core": out["fp32"], "speedup_tc_over_fp32": out["tc"]["value"] / out["fp32"]["value"],
+            "counts_identical": same, "counts_compared_on_queries": common, "tensor_core_recheck": recheck}
 
 
 def run_c3(args):
     """Halfspace depth at d=50: split-BF16x3 tensor-core path against the FP32 CUDA-core path."""
     from __graft_entry__ import build
     build()
-    h = measure_halfspace(args.nq or 10_000, args.steps, args.warmup)
+    h = measure_halfspace(args.nq or 10_000, args.steps, args.warmup, nq_fp32=min(args.nq or 10_000, 1000))
     line = {"metric": METRIC, "value": h["tensor_core"]["value"], "unit": "query-depths/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": h["tensor_core"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
