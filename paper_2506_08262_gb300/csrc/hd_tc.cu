@@ -187,10 +187,10 @@ __device__ __noinline__ int ff_sign(const float* __restrict__ u, const float* __
 
 template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_hd_tc(const __grid_constant__ CUtensorMap xmap, const TaskDev* __restrict__ tasks,
+    k_hd_tc(const CUtensorMap* __restrict__ maps, const TaskDev* __restrict__ tasks,
             const SlotDev* __restrict__ slots, const DsDev* __restrict__ dsets, const float* __restrict__ U,
             const double* __restrict__ yz, const double* __restrict__ z64, ResDev* __restrict__ res,
-            int64_t* __restrict__ band_out, int* err, float gamma, float ffcoef, int nst)
+            int64_t* __restrict__ band_out, int* err, float gamma, int nst)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ TcShared sh;
@@ -207,8 +207,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (*(volatile const int*)err & ERR_TIMEOUT) return;   // another CTA already gave up
     const TaskDev T = tasks[blockIdx.x];
-    const DsDev D = dsets[slots[T.slot].ds];
+    const int dsi = slots[T.slot].ds;
+    const DsDev D = dsets[dsi];
+    // the tensor map of this task's dataset (one per dataset in device memory, so one launch serves the
+    // tasks of every dataset with the same K extent)
+    const CUtensorMap* xmap = maps + dsi;
     const int kp = D.kp, nchunk = kp / 64, d = D.d, ldx = D.ldx;
+    const float ffcoef = band_coef_ff(d);
     const int64_t n = D.n;
     const int ntiles = (int)((n + BN - 1) / BN);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -336,6 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) {
         // ---- TMA producer ------------------------------------------------------------------
         if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)xmap) : "memory");
             int issued = 0;
             for (int t = 0; t < ntiles; ++t) {
                 const int s = t % nst;
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_arrive_expect_tx(&sh.full[s], 2 * b_plane);
                 for (int p = 0; p < 2; ++p)
                     for (int c = 0; c < nchunk; ++c)
-                        tma_load_2d(st + p * b_plane + c * plane_bytes_rows(BN), &xmap, p * kp + c * 64, t * BN,
+                        tma_load_2d(st + p * b_plane + c * plane_bytes_rows(BN), xmap, p * kp + c * 64, t * BN,
                                     &sh.full[s]);
                 issued = t + 1;
             }
@@ -711,7 +717,7 @@ float band_gamma_tc(int kp)
     return (float)(1.25 * g);
 }
 
-float band_coef_ff(int d)
+__host__ __device__ float band_coef_ff(int d)
 {
     // compensated FP32 dot product of d terms: the rounding errors of the gathered error terms,
     // at most (2d^2 + 4d + 8) 2^-48 sum|u x|; y_z's FP64 evaluation and its FP32 pair, at most
@@ -731,26 +737,31 @@ cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx
     return cudaGetLastError();
 }
 
-cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds_dev,
-                         const DsDev& ds_host, const float* U, const double* yz, const double* z64, ResDev* res,
-                         int64_t* band_out, int* err, cudaStream_t st)
+cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out)
 {
-    if (ntasks <= 0) return cudaSuccess;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const int kp = ds_host.kp;
     if (kp != 64 && kp != 128) return cudaErrorInvalidValue;
     if (ds_host.n > 0x7FFFFFFF) return cudaErrorInvalidValue;   // point indices and TMA rows are 32-bit
-    CUtensorMap map;
+    // the BF16 planes of this dataset only (no multicast): rows of 2 kp elements, boxes of 64 x BN
     const cuuint64_t gdim[2] = {(cuuint64_t)(2 * kp), (cuuint64_t)ds_host.n};
     const cuuint64_t gstride[1] = {(cuuint64_t)(2 * kp) * sizeof(uint16_t)};
-    const int bn = tc_tile_n(kp);
-    const cuuint32_t box[2] = {64, (cuuint32_t)bn};
+    const cuuint32_t box[2] = {64, (cuuint32_t)tc_tile_n(kp)};
     const cuuint32_t estride[2] = {1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ds_host.Xbf, gdim, gstride, box, estride,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ds_host.Xbf, gdim, gstride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, const SlotDev* slots, const DsDev* ds_dev,
+                         const CUtensorMap* maps, const float* U, const double* yz, const double* z64, ResDev* res,
+                         int64_t* band_out, int* err, cudaStream_t st)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    if (kp != 64 && kp != 128) return cudaErrorInvalidValue;
+    const int bn = tc_tile_n(kp);
     const size_t smem = tc_smem_bytes(kp);
     auto kern = bn == 256 ? k_hd_tc<256> : k_hd_tc<128>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -758,8 +769,8 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots,
         cudaGetLastError();
         return e;
     }
-    kern<<<ntasks, NTHREADS, smem, st>>>(map, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
-                                         band_gamma_tc(kp), band_coef_ff(ds_host.d), tc_stages(kp));
+    kern<<<ntasks, NTHREADS, smem, st>>>(maps, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
+                                         band_gamma_tc(kp), tc_stages(kp));
     return cudaGetLastError();
 }
 

@@ -151,14 +151,17 @@ struct Plan {
     int rmax = 0;
     int max_ldx = 4;
     int64_t tot_ldx = 0, tot_d = 0, tot_u = 0, tot_m = 0;
-    // tensor-core halfspace tasks, one group per dataset (one tensor map per launch)
+    // tensor-core halfspace tasks, one group per K extent of the planes (64 or 128), each group one launch
+    // per round whatever the datasets: every task's CTA takes its dataset's tensor map from maps
     struct TcGroup {
-        int ds = 0;
+        int kp = 0;
         std::vector<TaskDev> tasks;
         std::vector<int> n;   // active prefix per round
         TaskDev* d = nullptr;
     };
     std::vector<TcGroup> tc;
+    std::vector<CUtensorMap> maps;     // one per dataset row (encoded for datasets with tensor-core tasks)
+    CUtensorMap* d_maps = nullptr;
     // selection-kernel group size: autotuned choices and an explicit override (tuning probes)
     const std::map<std::tuple<int64_t, int, int>, int>* tune = nullptr;
     int force_group = 0;
@@ -332,13 +335,21 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
         if (tc) {
             // tensor-core tasks: 128 consecutive (query, direction) rows of this request, so the
             // accumulator's M dimension is filled across queries (task = first query slot, offset
-            // into that query's directions, row count); one task list per dataset
+            // into that query's directions, row count); one task list per K extent, and the dataset's
+            // tensor map in the plan's map table
             const int dsi = dsidx[R.dset];
+            const int kp = P.ds[dsi].kp;
+            if (P.maps.size() < P.ds.size()) P.maps.resize(P.ds.size());
+            if (P.ds[dsi].Xbf) {
+                static const CUtensorMap zero{};
+                if (!memcmp(&P.maps[dsi], &zero, sizeof zero) && encode_tc_map(P.ds[dsi], &P.maps[dsi]) != cudaSuccess)
+                    return fail(RRS_ERR_CUDA, "tensor map of dataset row %d", dsi);
+            }
             size_t gi = 0;
-            while (gi < P.tc.size() && P.tc[gi].ds != dsi) ++gi;
+            while (gi < P.tc.size() && P.tc[gi].kp != kp) ++gi;
             if (gi == P.tc.size()) {
                 P.tc.emplace_back();
-                P.tc.back().ds = dsi;
+                P.tc.back().kp = kp;
             }
             const int64_t rows = R.nq * (int64_t)m;
             for (int64_t g = 0; g < rows; g += 128)
@@ -387,6 +398,7 @@ size_t carve_plan(Plan& P, Carve& C)
     P.d_gen = C.take<TaskDev>(P.gen_tasks.size());
     P.d_hd = C.take<TaskDev>(P.hd_tasks.size());
     for (auto& g : P.tc) g.d = C.take<TaskDev>(g.tasks.size());
+    P.d_maps = P.maps.empty() ? nullptr : C.take<CUtensorMap>(P.maps.size());
     P.d_pd.resize(P.pd_tasks.size());
     for (size_t c = 0; c < P.pd_tasks.size(); ++c) P.d_pd[c] = C.take<TaskDev>(P.pd_tasks[c].size());
     P.d_arg = C.take<int32_t>(P.argmin_list.size());
@@ -413,6 +425,7 @@ rrs_status upload_plan(rrs_ctx* ctx, Plan& P, cudaStream_t st)
     CUDA_TRY(up(P.d_gen, P.gen_tasks.data(), P.gen_tasks.size() * sizeof(TaskDev)));
     CUDA_TRY(up(P.d_hd, P.hd_tasks.data(), P.hd_tasks.size() * sizeof(TaskDev)));
     for (auto& g : P.tc) CUDA_TRY(up(g.d, g.tasks.data(), g.tasks.size() * sizeof(TaskDev)));
+    if (P.d_maps) CUDA_TRY(up(P.d_maps, P.maps.data(), P.maps.size() * sizeof(CUtensorMap)));
     for (size_t c = 0; c < P.pd_tasks.size(); ++c)
         CUDA_TRY(up(P.d_pd[c], P.pd_tasks[c].data(), P.pd_tasks[c].size() * sizeof(TaskDev)));
     CUDA_TRY(up(P.d_arg, P.argmin_list.data(), P.argmin_list.size() * sizeof(int32_t)));
@@ -448,7 +461,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
         for (auto& g : P.tc) {
             if (g.n[l] <= 0) continue;
             StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
-            CUDA_TRY(launch_hd_tc(g.d, g.n[l], P.d_slots, P.d_ds, P.ds[g.ds], P.U, P.yz, P.z64, P.res, nullptr,
+            CUDA_TRY(launch_hd_tc(g.d, g.n[l], g.kp, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz, P.z64, P.res, nullptr,
                                   ctx->d_err, st));
             ctx->stage_launches[RRS_STAGE_HD_TC]++;
             ctx->launches++;
@@ -960,7 +973,7 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
         trace("debug_round_depths: y_z done");
         if (kind == RRS_HALFSPACE) {
             if (precision == RRS_PREC_SPLIT_BF16X3)
-                CUDA_TRY(launch_hd_tc(P.tc[0].d, (int)P.tc[0].tasks.size(), P.d_slots, P.d_ds, P.ds[0], P.U, P.yz,
+                CUDA_TRY(launch_hd_tc(P.tc[0].d, (int)P.tc[0].tasks.size(), P.tc[0].kp, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz,
                                       P.z64, P.res, band, ctx->d_err, st));
             else
                 CUDA_TRY(launch_hd_simt(P.d_hd, (int)P.hd_tasks.size(), P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz,

@@ -91,7 +91,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_fn();
-float band_coef_ff(int d);   // bound coefficient of the compensated FP32 re-check (tensor-core path)
+__host__ __device__ float band_coef_ff(int d);   // bound coefficient of the compensated FP32 re-check (tensor-core path)
 
 // Set the text that rrs_last_error() returns on this thread (rrs_api.cu).
 void set_last_error(const char* msg);
@@ -174,9 +174,13 @@ PdapShape pdap_shape(int n, int ldx, int m, int d, int group = 0);
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
                                      cudaStream_t st);
-// tasks of up to 128 directions of slots that all use the dataset ds_host (host copy of ds_dev[0..])
-cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, const SlotDev* slots, const DsDev* ds_dev,
-                         const DsDev& ds_host, const float* U, const double* yz, const double* z64, ResDev* res,
+// The tensor map of a dataset's BF16 planes (kp 64 or 128; planes built) for launch_hd_tc, written to *out
+// (host memory; the caller copies it into the device array passed as maps).
+cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out);
+// tasks of up to 128 (query, direction) rows each, of any datasets whose planes have K extent kp; maps[ds]
+// is the tensor map of dataset row ds of ds_dev (device memory, 64-byte aligned)
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, const SlotDev* slots, const DsDev* ds_dev,
+                         const CUtensorMap* maps, const float* U, const double* yz, const double* z64, ResDev* res,
                          int64_t* band_out, int* err, cudaStream_t st);
 bool hd_tc_supported(int d);
 cudaError_t launch_wait_probe(int* err, long long limit_cycles, cudaStream_t st);

@@ -117,6 +117,7 @@ struct rrs_server {
     double *d_z64 = nullptr, *d_yz = nullptr;
     ResDev* d_res = nullptr;
     DsDev* d_ds = nullptr;
+    CUtensorMap* d_maps = nullptr;   // tensor map of each dataset row with BF16 planes (tensor-core halfspace)
     int ds_cap = 0;
     char* d_tab = nullptr;      // per-step tables (tasks, lists, new slots)
     size_t tab_bytes = 0;
@@ -173,6 +174,12 @@ rrs_status ensure_dataset(rrs_server* S, int64_t id, int* row)
     const int r = (int)S->ds_host.size();
     S->ds_host.push_back(dd);
     S_TRY(cudaMemcpyAsync(S->d_ds + r, &S->ds_host[r], sizeof(DsDev), cudaMemcpyHostToDevice, S->st));
+    if (dd.Xbf) {
+        CUtensorMap map;
+        S_TRY(encode_tc_map(dd, &map));
+        S_TRY(cudaMemcpyAsync(S->d_maps + r, &map, sizeof map, cudaMemcpyHostToDevice, S->st));
+        S_TRY(cudaStreamSynchronize(S->st));   // the host copy of the map goes out of scope here
+    }
     S->ds_index[id] = r;
     *row = r;
     return RRS_OK;
@@ -287,7 +294,7 @@ rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_p
                  o_p0 = take(sizeof(float) * c * S->max_ldx), o_p1 = take(sizeof(float) * c * S->max_ldx),
                  o_z64 = take(sizeof(double) * c * max_d), o_U = take(sizeof(float) * c * S->max_m * S->max_ldx),
                  o_yz = take(sizeof(double) * c * S->max_m), o_res = take(sizeof(ResDev) * c * S->max_m),
-                 o_ds = take(sizeof(DsDev) * S->ds_cap);
+                 o_ds = take(sizeof(DsDev) * S->ds_cap), o_maps = take(sizeof(CUtensorMap) * S->ds_cap);
     if (ctx->budget && ctx->used + off > ctx->budget) {
         delete S;
         return sfail(RRS_ERR_BUDGET, "server arena needs %zu bytes", off);
@@ -310,6 +317,7 @@ rrs_status rrs_server_create(rrs_ctx* ctx, int32_t max_slots, int32_t max_dirs_p
     S->d_yz = (double*)(B + o_yz);
     S->d_res = (ResDev*)(B + o_res);
     S->d_ds = (DsDev*)(B + o_ds);
+    S->d_maps = (CUtensorMap*)(B + o_maps);
     for (int i = max_slots - 1; i >= 0; --i) S->free_slots.push_back(i);
     *out = S;
     return RRS_OK;
@@ -392,7 +400,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         for (size_t i = 0; i < na && capped && used < S->work_limit; ++i) take(i, 1.0);
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
-        std::map<int, std::vector<TaskDev>> tc;   // dataset row -> tensor-core halfspace tasks
+        std::map<int, std::vector<TaskDev>> tc;   // K extent of the planes -> tensor-core halfspace tasks
         // selection lists per (shared-memory class, G, kernel variant, dataset row for keys by k_keys or -1);
         // each launch requests the largest shared-memory need of its list
         std::map<std::tuple<size_t, int, int, int>, std::vector<TaskDev>> pd;
@@ -422,7 +430,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 for (int j0 = 0; j0 < R->m; j0 += 128) gen.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
                 if (use_tc) {
                     // slots of a request need not be adjacent: one task never crosses a slot
-                    auto& v = tc[row];
+                    auto& v = tc[D.kp];
                     for (int j0 = 0; j0 < R->m; j0 += 128) v.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
                 } else if (R->kind == RRS_HALFSPACE) {
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
@@ -464,8 +472,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         S_TRY(launch_hd_simt((const TaskDev*)(T + o_hd), (int)hd.size(), S->max_ldx, S->d_slots, S->d_ds, S->d_U,
                              S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err, S->st));
         for (auto& to : o_tc)
-            S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), S->d_slots, S->d_ds,
-                               S->ds_host[to.second], S->d_U, S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err,
+            S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), to.second, S->d_slots,
+                               S->d_ds, S->d_maps, S->d_U, S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err,
                                S->st));
         size_t extra = 0;
         for (auto& po : o_pd) {

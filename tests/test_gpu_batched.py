@@ -174,6 +174,16 @@ def test_batched_tensor_core_halfspace(ctx):
                 np.testing.assert_array_equal(outs[i]["count"].cpu().numpy(), cnt.cpu().numpy())
                 d32, c32, _, _ = ctx.depth(ids[i], outs[i]["Z"], 0, P.k, P.r, P.alpha, P.seed + i, rounds=True)
                 np.testing.assert_array_equal(outs[i]["count"].cpu().numpy(), c32.cpu().numpy())
+    # one tensor-core launch per round and K extent of the planes (64 or 128), whatever the datasets: each
+    # CTA takes its dataset's tensor map from the device table
+    kps = {64 if P.d + 2 <= 64 else 128 for P in problems if P.kind == 0}
+    rrs.rrs_profile_enable(ctx.handle, True)
+    rrs.rrs_depth_batched(ctx.handle, reqs, use_graph=False, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    prof = rrs.rrs_profile_read(ctx.handle)
+    rrs.rrs_profile_enable(ctx.handle, False)
+    rounds = max(P.r for P in problems if P.kind == 0)
+    assert prof["hd_tc"][1] == rounds * len(kps), (prof["hd_tc"], kps)
     for did in ids:
         ctx.free(did)
 
