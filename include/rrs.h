@@ -177,12 +177,15 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
  * rrs_autotune - pick the selection kernel for projection / asymmetric
  * projection depth on this dataset with m = ceil(n_dirs / n_refinements)
  * directions per round: 1, 2 or 4 directions per CTA with the keys held in
- * shared memory, or RRS_SELECT_WARP (one warp per direction, keys re-formed
- * from X at every pass; d <= 16 and n <= 12,288).  Each feasible choice is
+ * shared memory, RRS_SELECT_STREAM (keys formed once per round in device
+ * memory and read at every pass), or RRS_SELECT_WARP (one warp per direction,
+ * keys re-formed from X at every pass; d <= 16 and n <= 12,288).  Each
+ * feasible choice is
  * timed on one round of probe queries (rows of the dataset, two per SM) and
  * the fastest is cached in the context; later rrs_depth / rrs_depth_batched
- * calls with the same (n, d, m) use it.  Without tuning a shared-memory
- * heuristic picks among the kernels that hold the keys.  Results
+ * calls with the same (n, d, m) use it.  Without tuning: two or more
+ * directions per CTA with resident keys where that fits two CTAs per SM,
+ * else the streamed keys.  Results
  * never depend on the choice.  *choice_out (optional) receives it (0 for
  * halfspace depth, which has nothing to tune, and 0 when no choice keeps the
  * keys in shared memory: they then live in device memory and the kernel runs
@@ -190,14 +193,18 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
  * Synchronous.  Errors: INVALID_ARG, NOT_FOUND, CUDA.
  */
 #define RRS_SELECT_WARP 64
+#define RRS_SELECT_STREAM 32
 rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t n_dirs, int32_t n_refinements,
                         int32_t* choice_out);
 
 /*
  * rrs_select_kernel - fix the selection kernel for (this dataset's n and d,
  * m = ceil(n_dirs / n_refinements)) instead of timing it: choice 1, 2 or 4
- * (directions per CTA, keys in shared memory), RRS_SELECT_WARP, or 0 to drop a
- * fixed or tuned choice and return to the default.  A choice that does not
+ * (directions per CTA, keys in shared memory), RRS_SELECT_WARP,
+ * RRS_SELECT_STREAM, or 0 to drop a
+ * fixed or tuned choice and return to the default; RRS_SELECT_STREAM keeps the
+ * keys outside shared memory (formed once per round by a keys kernel, read
+ * at every pass) whatever n.  A choice that does not
  * fit the dataset falls back to the default at launch.  Results never depend
  * on the choice.  Errors: INVALID_ARG (NULL context, unknown choice),
  * NOT_FOUND.

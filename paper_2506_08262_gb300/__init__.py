@@ -36,6 +36,7 @@ RRS_F32, RRS_F64 = 0, 1
 RRS_HALFSPACE, RRS_PROJECTION, RRS_ASYM_PROJECTION = 0, 1, 2
 RRS_PREC_FP32_SIMT, RRS_PREC_SPLIT_BF16X3 = 0, 1
 RRS_SELECT_WARP = 64
+RRS_SELECT_STREAM = 32
 
 
 class RRSError(RuntimeError):
@@ -307,7 +308,8 @@ def rrs_autotune(ctx: int, dataset_id: int, kind: int, n_dirs: int, n_refinement
 
 
 def rrs_select_kernel(ctx: int, dataset_id: int, n_dirs: int, n_refinements: int, choice: int) -> None:
-    """Fix the selection kernel (1, 2, 4 directions per CTA, RRS_SELECT_WARP, or 0 for the default)."""
+    """Fix the selection kernel (1, 2, 4 directions per CTA, RRS_SELECT_WARP, RRS_SELECT_STREAM, or 0 for
+    the default)."""
     _check(load().rrs_select_kernel(ctx, dataset_id, n_dirs, n_refinements, choice), "rrs_select_kernel")
 
 

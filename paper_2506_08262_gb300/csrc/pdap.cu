@@ -1626,13 +1626,16 @@ size_t pdap_two_per_sm_limit()
     return 112 * 1024;
 }
 
-int pdap_max_group(int n, int ldx, int m, int d, bool keys_in)
+int pdap_max_group(int n, int ldx, int m, int d, bool keys_in, bool allow_stream)
 {
-    // G in {1, 2, 4}: the largest G that fits two CTAs per SM when that is at least 2, else the
-    // largest that fits one CTA per SM.  Exception: for d > 16 with keys formed inside the kernel
-    // the projection pass re-reads X (4 d bytes per point) for every G directions, so there the
-    // largest G that fits wins (measured at n = 10,000: d = 50 1.27x, d = 150 1.68x faster with
-    // G = 4 than G = 2); with keys from k_keys the usual rule holds again.
+    // G in {1, 2, 4}: the largest G that fits two CTAs per SM when that is at least 2.  Below that the
+    // keys go outside shared memory (0: formed once per round by a keys kernel, read at every pass),
+    // which keeps four directions per SM in flight instead of one or two (measured on the 256-dataset
+    // batched workload: the selection stage 8.2 s -> 5.4 s, identical results); callers that cannot
+    // hold the keys elsewhere (allow_stream false) take the largest G that fits one CTA per SM.
+    // Exception: for d > 16 with keys formed inside the kernel the projection pass re-reads X (4 d
+    // bytes per point) for every G directions, so there the largest G that fits wins (measured at
+    // n = 10,000: d = 50 1.27x, d = 150 1.68x faster with G = 4 than G = 2).
     const size_t one = pdap_smem_limit(), two = pdap_two_per_sm_limit();
     int g_one = 0, g_two = 0;
     for (int g = 1; g <= MAXG && g <= m; g *= 2) {
@@ -1641,8 +1644,8 @@ int pdap_max_group(int n, int ldx, int m, int d, bool keys_in)
         if (need <= two) g_two = g;
     }
     if (pdap_dp4_class(d) == 0 && !keys_in) return g_one;
-    if (g_two >= 2) return g_two;
-    return g_one;
+    if (g_two >= 2 || (g_two >= 1 && m < 2)) return g_two;
+    return allow_stream ? 0 : g_one;
 }
 
 // Keys of a block of tasks (G directions each, all of one dataset) for every point, as a tiled FP32
@@ -1879,9 +1882,9 @@ PdapShape pdap_shape(int n, int ldx, int m, int d, int group)
         s.keys_gemm = false;
         return s;
     }
-    int G = group == PDAP_WARP_GROUP ? 0 : group;
+    int G = (group == PDAP_WARP_GROUP || group == PDAP_STREAM_CHOICE) ? 0 : group;
     if (G && (G > m || pdap_smem_bytes(n, G, ldx) > pdap_smem_limit())) G = 0;
-    if (!G) G = pdap_max_group(n, ldx, m, d, dp4 == 0);
+    if (!G && group != PDAP_STREAM_CHOICE) G = pdap_max_group(n, ldx, m, d, dp4 == 0, true);
     if (G) {
         s.group = G;
         s.variant = dp4;

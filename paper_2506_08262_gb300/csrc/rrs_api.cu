@@ -1057,9 +1057,10 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     CUDA_TRY(cudaEventCreate(&b));
     int best = 0;
     float best_ms = 0.0f;
-    for (int G : {1, 2, 4, PDAP_WARP_GROUP}) {
+    for (int G : {1, 2, 4, PDAP_WARP_GROUP, PDAP_STREAM_CHOICE}) {
         if (G == PDAP_WARP_GROUP ? !pdapw_eligible(D.n, D.d)
-                                 : (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit()))
+                                 : (G != PDAP_STREAM_CHOICE &&
+                                    (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())))
             continue;
         ReqView R{};
         R.dset = &D;
@@ -1102,7 +1103,8 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
 rrs_status rrs_select_kernel(rrs_ctx* ctx, int64_t dataset_id, int32_t n_dirs, int32_t n_refinements, int32_t choice)
 {
     if (!ctx) return fail(RRS_ERR_INVALID_ARG, "NULL context");
-    if (choice != 0 && choice != 1 && choice != 2 && choice != 4 && choice != PDAP_WARP_GROUP)
+    if (choice != 0 && choice != 1 && choice != 2 && choice != 4 && choice != PDAP_WARP_GROUP &&
+        choice != PDAP_STREAM_CHOICE)
         return fail(RRS_ERR_INVALID_ARG, "unknown selection kernel choice %d", choice);
     if (n_refinements < 1 || n_dirs < n_refinements) return fail(RRS_ERR_INVALID_ARG, "need n_dirs >= n_refinements >= 1");
     std::lock_guard<std::mutex> lk(ctx->mu);

@@ -143,7 +143,8 @@ cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* c
 cudaError_t launch_check_finite(const void* Z, int dtype, int64_t count, int* bad, cudaStream_t st);
 size_t pdap_smem_bytes(int n, int group, int ldx, bool stream = false);
 size_t pdap_smem_limit();
-int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false);   // preferred resident G (0 if none fits)
+// preferred resident G; 0: keys outside shared memory (when allow_stream, or when none fits)
+int pdap_max_group(int n, int ldx, int m, int d, bool keys_in = false, bool allow_stream = false);
 
 // Selection-kernel variant bit: the keys are not held in shared memory (n beyond what shared memory holds
 // for one direction); every pass reads them from k_keys output in global memory when given (kin), else
@@ -159,6 +160,8 @@ constexpr int PDAP_WARP = 0x200;
 constexpr int PDAPW_DIRS = 12;
 constexpr int64_t PDAPW_MAX_N = 12288;
 constexpr int PDAP_WARP_GROUP = RRS_SELECT_WARP;
+// pdap_shape group asking for the keys outside shared memory (formed once per round, read at every pass)
+constexpr int PDAP_STREAM_CHOICE = RRS_SELECT_STREAM;
 size_t pdapw_smem_bytes(int d);
 bool pdapw_eligible(int64_t n, int d);
 struct PdapShape {

@@ -359,7 +359,7 @@ def test_autotuned_group_does_not_change_results(ctx, kind):
     Zt = torch.from_numpy(Z).cuda()
     before = ctx.depth(did, Zt, kind, 100, 4, 0.7, 3)[0].cpu().numpy()
     g = rrs.rrs_autotune(ctx.handle, did, kind, 100, 4)
-    assert g in (1, 2, 4, rrs.RRS_SELECT_WARP)
+    assert g in (1, 2, 4, rrs.RRS_SELECT_WARP, rrs.RRS_SELECT_STREAM)
     after = ctx.depth(did, Zt, kind, 100, 4, 0.7, 3)[0].cpu().numpy()
     ctx.free(did)
     np.testing.assert_array_equal(before, after)
@@ -369,15 +369,15 @@ def test_autotuned_group_does_not_change_results(ctx, kind):
 @pytest.mark.parametrize("n,d,m", [(3001, 10, 50), (777, 5, 37), (12288, 16, 25), (9000, 3, 13), (40, 7, 24),
                                    (2, 4, 12)])
 def test_every_selection_kernel_selects_the_same_points(ctx, kind, n, d, m):
-    # the warp-per-direction kernel (keys re-formed at every pass) and the shared-memory kernels with 1, 2 or
-    # 4 directions per CTA rank the same FP32 keys by (value, index) and form the depth from the same FP64
-    # projections: bit-identical depths and per-round choices whatever kernel runs
+    # the warp-per-direction kernel (keys re-formed at every pass), the shared-memory kernels with 1, 2 or 4
+    # directions per CTA and the streamed-keys kernel rank the same FP32 keys by (value, index) and form the
+    # depth from the same FP64 projections: bit-identical depths and per-round choices whatever kernel runs
     X, Z = workloads.gaussian_cloud(n + 7 * d + m, n, d, 9, dtype=np.float32)
     did = ctx.register(torch.from_numpy(X).cuda())
     Zt = torch.from_numpy(Z).cuda()
     k, r = 3 * m, 3
     out = {}
-    for choice in (0, 1, 2, 4, rrs.RRS_SELECT_WARP):
+    for choice in (0, 1, 2, 4, rrs.RRS_SELECT_WARP, rrs.RRS_SELECT_STREAM):
         rrs.rrs_select_kernel(ctx.handle, did, k, r, choice)
         dep, _, best, ch = ctx.depth(did, Zt, kind, k, r, 0.6, 4, rounds=True)
         out[choice] = (dep.cpu().numpy(), best.cpu().numpy(), ch.cpu().numpy())
