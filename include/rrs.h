@@ -174,8 +174,11 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
                              int32_t use_graph, void* stream);
 
 /*
- * rrs_autotune - pick the selection kernel for projection / asymmetric
- * projection depth on this dataset with m = ceil(n_dirs / n_refinements)
+ * rrs_autotune - for halfspace depth on the tensor cores, pick the tile width
+ * (128 or 256 points per tile; planes of K extent 64 only, other d have one
+ * width) and cache it per (n, d); *choice_out receives it (0 when d has no
+ * tensor-core path).  For projection / asymmetric projection depth, pick the
+ * selection kernel on this dataset with m = ceil(n_dirs / n_refinements)
  * directions per round: 1, 2 or 4 directions per CTA with the keys held in
  * shared memory, RRS_SELECT_STREAM (keys formed once per round in device
  * memory and read at every pass), or RRS_SELECT_WARP (one warp per direction,
@@ -211,6 +214,17 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
  */
 rrs_status rrs_select_kernel(rrs_ctx* ctx, int64_t dataset_id, int32_t n_dirs, int32_t n_refinements,
                              int32_t choice);
+
+/*
+ * rrs_select_tc_tile - fix the tensor-core halfspace tile width for this
+ * dataset's (n, d): 128 or 256 points per tile (256 exists only for planes of
+ * K extent 64, i.e. d + 2 <= 64; a width that does not exist falls back to the
+ * one that does), or 0 for the default (256 where it exists).  Counts never
+ * depend on the width.  Cached graphs of batched calls are dropped, since they
+ * replay the width of their capture; rrs_select_kernel and rrs_autotune do the
+ * same.  Errors: INVALID_ARG, NOT_FOUND, UNSUPPORTED (d + 2 > 128).
+ */
+rrs_status rrs_select_tc_tile(rrs_ctx* ctx, int64_t dataset_id, int32_t tile_points);
 
 /* Text for a status code (static storage). */
 const char* rrs_status_string(rrs_status status);

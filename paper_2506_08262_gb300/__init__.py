@@ -92,6 +92,7 @@ _SIGS = {
                       ctypes.c_void_p], ctypes.c_int32),
     "rrs_select_kernel": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
                           ctypes.c_int32),
+    "rrs_select_tc_tile": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32], ctypes.c_int32),
     "rrs_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int32),
     "rrs_launch_count": ([ctypes.c_void_p], ctypes.c_uint64),
     "rrs_profile_enable": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int32),
@@ -301,7 +302,8 @@ def rrs_debug_wait_timeout(ctx: int, limit_cycles: int) -> None:
 
 
 def rrs_autotune(ctx: int, dataset_id: int, kind: int, n_dirs: int, n_refinements: int) -> int:
-    """Time the selection kernel's group sizes for this (dataset, kind, m) and cache the fastest."""
+    """Time the selection kernels (projection depths) or the tensor-core tile widths (halfspace) for this
+    dataset and cache the fastest; returns the choice."""
     choice = ctypes.c_int32()
     _check(load().rrs_autotune(ctx, dataset_id, kind, n_dirs, n_refinements, ctypes.byref(choice)), "rrs_autotune")
     return choice.value
@@ -311,6 +313,11 @@ def rrs_select_kernel(ctx: int, dataset_id: int, n_dirs: int, n_refinements: int
     """Fix the selection kernel (1, 2, 4 directions per CTA, RRS_SELECT_WARP, RRS_SELECT_STREAM, or 0 for
     the default)."""
     _check(load().rrs_select_kernel(ctx, dataset_id, n_dirs, n_refinements, choice), "rrs_select_kernel")
+
+
+def rrs_select_tc_tile(ctx: int, dataset_id: int, tile_points: int) -> None:
+    """Fix the tensor-core halfspace tile width (128 or 256 points, or 0 for the default)."""
+    _check(load().rrs_select_tc_tile(ctx, dataset_id, tile_points), "rrs_select_tc_tile")
 
 
 def rrs_check(ctx: int, stream=None) -> None:

@@ -674,15 +674,14 @@ EncodeTiledFn encode_fn()
 
 namespace {
 
-int tc_tile_n(int kp) { return kp <= 64 ? 256 : 128; }
+// ring stages: 2 x 64 KB (K extent 64, 256 points; 128, 128 points), 4 x 32 KB (64, 128 points)
+int tc_stages(int kp, int bn) { return (kp == 64 && bn == 128) ? 4 : 2; }
 
-int tc_stages(int kp) { return 2; }   // 2 x 64 KB (K extent 64, 256 points) or 2 x 64 KB (128, 128 points)
-
-size_t tc_smem_bytes(int kp)
+size_t tc_smem_bytes(int kp, int bn)
 {
     const size_t nchunk = (size_t)kp / 64;
     return 1024 /* alignment slack */ + 2 * nchunk * plane_bytes_rows(BM) +
-           (size_t)tc_stages(kp) * 2 * nchunk * plane_bytes_rows(tc_tile_n(kp));
+           (size_t)tc_stages(kp, bn) * 2 * nchunk * plane_bytes_rows(bn);
 }
 
 // Failure-path check: one thread waits on an mbarrier that nothing will complete,
@@ -737,7 +736,15 @@ cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx
     return cudaGetLastError();
 }
 
-cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out)
+int tc_tile_n(int kp, int want)
+{
+    // 256 points per tile for a K extent of 64 (a 128 x 256 x 16 MMA runs at the full tensor rate, 128 x 128 x 16
+    // does not), unless 128 is asked for; 128 for a K extent of 128 (two 256-point stages would not fit)
+    if (kp <= 64) return want == 128 ? 128 : 256;
+    return 128;
+}
+
+cudaError_t encode_tc_map(const DsDev& ds_host, int bn, CUtensorMap* out)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -747,7 +754,8 @@ cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out)
     // the BF16 planes of this dataset only (no multicast): rows of 2 kp elements, boxes of 64 x BN
     const cuuint64_t gdim[2] = {(cuuint64_t)(2 * kp), (cuuint64_t)ds_host.n};
     const cuuint64_t gstride[1] = {(cuuint64_t)(2 * kp) * sizeof(uint16_t)};
-    const cuuint32_t box[2] = {64, (cuuint32_t)tc_tile_n(kp)};
+    if (bn != tc_tile_n(kp, bn)) return cudaErrorInvalidValue;
+    const cuuint32_t box[2] = {64, (cuuint32_t)bn};
     const cuuint32_t estride[2] = {1, 1};
     const CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ds_host.Xbf, gdim, gstride, box, estride,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -755,14 +763,14 @@ cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out)
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, const SlotDev* slots, const DsDev* ds_dev,
-                         const CUtensorMap* maps, const float* U, const double* yz, const double* z64, ResDev* res,
-                         int64_t* band_out, int* err, cudaStream_t st)
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, int bn, const SlotDev* slots,
+                         const DsDev* ds_dev, const CUtensorMap* maps, const float* U, const double* yz,
+                         const double* z64, ResDev* res, int64_t* band_out, int* err, cudaStream_t st)
 {
     if (ntasks <= 0) return cudaSuccess;
     if (kp != 64 && kp != 128) return cudaErrorInvalidValue;
-    const int bn = tc_tile_n(kp);
-    const size_t smem = tc_smem_bytes(kp);
+    if (bn != tc_tile_n(kp, bn)) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem_bytes(kp, bn);
     auto kern = bn == 256 ? k_hd_tc<256> : k_hd_tc<128>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
@@ -770,7 +778,7 @@ cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, const SlotDev
         return e;
     }
     kern<<<ntasks, NTHREADS, smem, st>>>(maps, tasks, slots, ds_dev, U, yz, z64, res, band_out, err,
-                                         band_gamma_tc(kp), tc_stages(kp));
+                                         band_gamma_tc(kp), tc_stages(kp, bn));
     return cudaGetLastError();
 }
 

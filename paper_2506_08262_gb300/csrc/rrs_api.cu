@@ -154,7 +154,7 @@ struct Plan {
     // tensor-core halfspace tasks, one group per K extent of the planes (64 or 128), each group one launch
     // per round whatever the datasets: every task's CTA takes its dataset's tensor map from maps
     struct TcGroup {
-        int kp = 0;
+        int kp = 0, bn = 0;   // K extent of the planes, points per tile
         std::vector<TaskDev> tasks;
         std::vector<int> n;   // active prefix per round
         TaskDev* d = nullptr;
@@ -164,6 +164,7 @@ struct Plan {
     CUtensorMap* d_maps = nullptr;
     // selection-kernel group size: autotuned choices and an explicit override (tuning probes)
     const std::map<std::tuple<int64_t, int, int>, int>* tune = nullptr;
+    const std::map<std::pair<int64_t, int>, int>* tc_tune = nullptr;   // (n, kp) -> points per tile
     int force_group = 0;
     // device pointers (after carving)
     DsDev* d_ds = nullptr;
@@ -339,17 +340,25 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
             // tensor map in the plan's map table
             const int dsi = dsidx[R.dset];
             const int kp = P.ds[dsi].kp;
+            int want = 0;
+            if (P.tc_tune) {
+                auto it = P.tc_tune->find(std::make_pair(P.ds[dsi].n, kp));
+                if (it != P.tc_tune->end()) want = it->second;
+            }
+            const int bn = tc_tile_n(kp, want);
             if (P.maps.size() < P.ds.size()) P.maps.resize(P.ds.size());
             if (P.ds[dsi].Xbf) {
                 static const CUtensorMap zero{};
-                if (!memcmp(&P.maps[dsi], &zero, sizeof zero) && encode_tc_map(P.ds[dsi], &P.maps[dsi]) != cudaSuccess)
+                if (!memcmp(&P.maps[dsi], &zero, sizeof zero) &&
+                    encode_tc_map(P.ds[dsi], bn, &P.maps[dsi]) != cudaSuccess)
                     return fail(RRS_ERR_CUDA, "tensor map of dataset row %d", dsi);
             }
             size_t gi = 0;
-            while (gi < P.tc.size() && P.tc[gi].kp != kp) ++gi;
+            while (gi < P.tc.size() && (P.tc[gi].kp != kp || P.tc[gi].bn != bn)) ++gi;
             if (gi == P.tc.size()) {
                 P.tc.emplace_back();
                 P.tc.back().kp = kp;
+                P.tc.back().bn = bn;
             }
             const int64_t rows = R.nq * (int64_t)m;
             for (int64_t g = 0; g < rows; g += 128)
@@ -461,8 +470,8 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
         for (auto& g : P.tc) {
             if (g.n[l] <= 0) continue;
             StageTimer t(ctx, RRS_STAGE_HD_TC, st, capturing);
-            CUDA_TRY(launch_hd_tc(g.d, g.n[l], g.kp, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz, P.z64, P.res, nullptr,
-                                  ctx->d_err, st));
+            CUDA_TRY(launch_hd_tc(g.d, g.n[l], g.kp, g.bn, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz, P.z64, P.res,
+                                  nullptr, ctx->d_err, st));
             ctx->stage_launches[RRS_STAGE_HD_TC]++;
             ctx->launches++;
         }
@@ -684,10 +693,25 @@ rrs_status rrs::ensure_bf16_planes(rrs_ctx* ctx, Dataset& D)
     return RRS_OK;
 }
 
+// Cached graphs replay the kernel choices of their capture: a changed choice drops them (after the device is
+// idle, so none is in flight).
+static void drop_graphs(rrs_ctx* ctx)
+{
+    if (ctx->graphs.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto& g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        cudaFree(g.ws);
+    }
+    ctx->graphs.clear();
+    cudaGetLastError();
+}
+
 static rrs_status run_requests(rrs_ctx* ctx, std::vector<ReqView>& reqs, cudaStream_t st, int force_group = 0)
 {
     Plan P;
     P.tune = &ctx->pd_tune;
+    P.tc_tune = &ctx->tc_tune;
     P.force_group = force_group;
     rrs_status s = build_plan(reqs, P);
     if (s != RRS_OK) return s;
@@ -854,6 +878,7 @@ rrs_status rrs_depth_batched(rrs_ctx* ctx, const rrs_request* reqs, int32_t n_re
     }
     Plan P;
     P.tune = &ctx->pd_tune;
+    P.tc_tune = &ctx->tc_tune;
     rrs_status s = build_plan(views, P);
     if (s != RRS_OK) return s;
     Carve sizing;
@@ -973,7 +998,7 @@ rrs_status rrs_debug_round_depths(rrs_ctx* ctx, int64_t dataset_id, const void* 
         trace("debug_round_depths: y_z done");
         if (kind == RRS_HALFSPACE) {
             if (precision == RRS_PREC_SPLIT_BF16X3)
-                CUDA_TRY(launch_hd_tc(P.tc[0].d, (int)P.tc[0].tasks.size(), P.tc[0].kp, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz,
+                CUDA_TRY(launch_hd_tc(P.tc[0].d, (int)P.tc[0].tasks.size(), P.tc[0].kp, P.tc[0].bn, P.d_slots, P.d_ds, P.d_maps, P.U, P.yz,
                                       P.z64, P.res, band, ctx->d_err, st));
             else
                 CUDA_TRY(launch_hd_simt(P.d_hd, (int)P.hd_tasks.size(), P.max_ldx, P.d_slots, P.d_ds, P.U, P.yz,
@@ -1031,12 +1056,21 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     rrs_status s = validate_params(kind, n_dirs, n_refinements, 0.5, RRS_F32, RRS_PREC_FP32_SIMT);
     if (s != RRS_OK) return s;
     if (choice_out) *choice_out = 0;
-    if (kind == RRS_HALFSPACE) return RRS_OK;   // nothing to tune on this path
     std::lock_guard<std::mutex> lk(ctx->mu);
     auto it = ctx->datasets.find(dataset_id);
     if (it == ctx->datasets.end()) return fail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)dataset_id);
     CUDA_TRY(cudaSetDevice(ctx->device));
     Dataset& D = it->second;
+    // halfspace: the tensor-core tile width where two exist (planes of K extent 64); the FP32 path has
+    // nothing to tune
+    if (kind == RRS_HALFSPACE && (!hd_tc_supported(D.d) || (int)align_up(D.d + 2, 64) != 64)) {
+        if (choice_out && hd_tc_supported(D.d)) *choice_out = tc_tile_n((int)align_up(D.d + 2, 64));
+        return RRS_OK;
+    }
+    if (kind == RRS_HALFSPACE) {
+        s = ensure_bf16_planes(ctx, D);
+        if (s != RRS_OK) return s;
+    }
     const int m = (n_dirs + n_refinements - 1) / n_refinements;
     const auto key = std::make_tuple(D.n, D.ldx, m);
     // probe queries: the first rows of the data cloud, 2 per SM
@@ -1057,11 +1091,16 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     CUDA_TRY(cudaEventCreate(&b));
     int best = 0;
     float best_ms = 0.0f;
-    for (int G : {1, 2, 4, PDAP_WARP_GROUP, PDAP_STREAM_CHOICE}) {
-        if (G == PDAP_WARP_GROUP ? !pdapw_eligible(D.n, D.d)
-                                 : (G != PDAP_STREAM_CHOICE &&
-                                    (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit())))
+    const bool hd = kind == RRS_HALFSPACE;
+    const auto tc_key = std::make_pair(D.n, 64);
+    const std::vector<int> cands = hd ? std::vector<int>{256, 128}
+                                      : std::vector<int>{1, 2, 4, PDAP_WARP_GROUP, PDAP_STREAM_CHOICE};
+    for (int G : cands) {
+        if (!hd && (G == PDAP_WARP_GROUP ? !pdapw_eligible(D.n, D.d)
+                                         : (G != PDAP_STREAM_CHOICE &&
+                                            (G > m || pdap_smem_bytes((int)D.n, G, D.ldx) > pdap_smem_limit()))))
             continue;
+        if (hd) ctx->tc_tune[tc_key] = G;
         ReqView R{};
         R.dset = &D;
         R.Z = zd;
@@ -1072,11 +1111,12 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
         R.r = 1;
         R.alpha = 0.5f;
         R.depth_out = dep;
+        if (hd) R.precision = RRS_PREC_SPLIT_BF16X3;
         float t = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             std::vector<ReqView> reqs{R};
             CUDA_TRY(cudaEventRecord(a, 0));
-            s = run_requests(ctx, reqs, 0, G);
+            s = run_requests(ctx, reqs, 0, hd ? 0 : G);
             if (s != RRS_OK) break;
             CUDA_TRY(cudaEventRecord(b, 0));
             CUDA_TRY(cudaEventSynchronize(b));
@@ -1094,8 +1134,15 @@ rrs_status rrs_autotune(rrs_ctx* ctx, int64_t dataset_id, int32_t kind, int32_t 
     cudaEventDestroy(b);
     cudaFree(zd);
     cudaFree(dep);
+    if (hd) ctx->tc_tune.erase(tc_key);
     if (s != RRS_OK) return s;
-    if (best) ctx->pd_tune[key] = best;
+    if (best) {
+        if (hd)
+            ctx->tc_tune[tc_key] = best;
+        else
+            ctx->pd_tune[key] = best;
+    }
+    drop_graphs(ctx);
     if (choice_out) *choice_out = best;
     return check_device_errors(ctx, 0);
 }
@@ -1117,6 +1164,27 @@ rrs_status rrs_select_kernel(rrs_ctx* ctx, int64_t dataset_id, int32_t n_dirs, i
         ctx->pd_tune.erase(key);
     else
         ctx->pd_tune[key] = choice;
+    drop_graphs(ctx);
+    return RRS_OK;
+}
+
+rrs_status rrs_select_tc_tile(rrs_ctx* ctx, int64_t dataset_id, int32_t tile_points)
+{
+    if (!ctx) return fail(RRS_ERR_INVALID_ARG, "NULL context");
+    if (tile_points != 0 && tile_points != 128 && tile_points != 256)
+        return fail(RRS_ERR_INVALID_ARG, "tile width %d: 0, 128 or 256", tile_points);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->datasets.find(dataset_id);
+    if (it == ctx->datasets.end()) return fail(RRS_ERR_NOT_FOUND, "no dataset %lld", (long long)dataset_id);
+    const Dataset& D = it->second;
+    if (!hd_tc_supported(D.d)) return fail(RRS_ERR_UNSUPPORTED, "d=%d has no tensor-core path", D.d);
+    const int kp = (D.d + 2 + 63) / 64 * 64;
+    const auto key = std::make_pair(D.n, kp);
+    if (tile_points == 0)
+        ctx->tc_tune.erase(key);
+    else
+        ctx->tc_tune[key] = tile_points;
+    drop_graphs(ctx);
     return RRS_OK;
 }
 

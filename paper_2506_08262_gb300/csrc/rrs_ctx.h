@@ -51,6 +51,7 @@ struct rrs_ctx {
     std::vector<GraphEntry> graphs;
     // selection-kernel autotuning: (n, ldx, m) -> directions per CTA
     std::map<std::tuple<int64_t, int, int>, int> pd_tune;
+    std::map<std::pair<int64_t, int>, int> tc_tune;   // (n, kp) -> points per tensor-core tile
     // per-stage CUDA-event timing (rrs_profile_*)
     bool profiling = false;
     struct Mark {

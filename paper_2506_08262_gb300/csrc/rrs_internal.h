@@ -177,14 +177,18 @@ PdapShape pdap_shape(int n, int ldx, int m, int d, int group = 0);
 // tensor-core path (hd_tc.cu)
 cudaError_t launch_build_bf16_planes(const float* X32, int64_t n, int d, int ldx, int kp, uint16_t* Xbf,
                                      cudaStream_t st);
-// The tensor map of a dataset's BF16 planes (kp 64 or 128; planes built) for launch_hd_tc, written to *out
+// Points per tile of the tensor-core kernel for planes of K extent kp: want = 128 or 256 where both exist
+// (kp = 64), anything else for the default.
+int tc_tile_n(int kp, int want = 0);
+// The tensor map of a dataset's BF16 planes (kp 64 or 128; planes built) for tiles of bn points, written to *out
 // (host memory; the caller copies it into the device array passed as maps).
-cudaError_t encode_tc_map(const DsDev& ds_host, CUtensorMap* out);
-// tasks of up to 128 (query, direction) rows each, of any datasets whose planes have K extent kp; maps[ds]
-// is the tensor map of dataset row ds of ds_dev (device memory, 64-byte aligned)
-cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, const SlotDev* slots, const DsDev* ds_dev,
-                         const CUtensorMap* maps, const float* U, const double* yz, const double* z64, ResDev* res,
-                         int64_t* band_out, int* err, cudaStream_t st);
+cudaError_t encode_tc_map(const DsDev& ds_host, int bn, CUtensorMap* out);
+// tasks of up to 128 (query, direction) rows each, of any datasets whose planes have K extent kp and whose maps
+// were encoded for tiles of bn points; maps[ds] is the tensor map of dataset row ds of ds_dev (device memory,
+// 64-byte aligned)
+cudaError_t launch_hd_tc(const TaskDev* tasks, int ntasks, int kp, int bn, const SlotDev* slots,
+                         const DsDev* ds_dev, const CUtensorMap* maps, const float* U, const double* yz,
+                         const double* z64, ResDev* res, int64_t* band_out, int* err, cudaStream_t st);
 bool hd_tc_supported(int d);
 cudaError_t launch_wait_probe(int* err, long long limit_cycles, cudaStream_t st);
 

@@ -130,6 +130,7 @@ struct rrs_server {
     std::vector<Request*> active;
     std::map<int64_t, int> ds_index;   // dataset id -> row of d_ds
     std::vector<DsDev> ds_host;
+    std::vector<int> ds_bn;            // tensor-core tile width of each dataset row (0: no planes)
     int64_t next_id = 1;
     int active_queries = 0;
     double work_limit = RRS_SERVER_DEFAULT_WORK;   // weighted pairs per step (0: every admitted query)
@@ -174,13 +175,17 @@ rrs_status ensure_dataset(rrs_server* S, int64_t id, int* row)
     const int r = (int)S->ds_host.size();
     S->ds_host.push_back(dd);
     S_TRY(cudaMemcpyAsync(S->d_ds + r, &S->ds_host[r], sizeof(DsDev), cudaMemcpyHostToDevice, S->st));
+    int bn = 0;
     if (dd.Xbf) {
+        auto t = S->ctx->tc_tune.find(std::make_pair(dd.n, dd.kp));
+        bn = tc_tile_n(dd.kp, t == S->ctx->tc_tune.end() ? 0 : t->second);
         CUtensorMap map;
-        S_TRY(encode_tc_map(dd, &map));
+        S_TRY(encode_tc_map(dd, bn, &map));
         S_TRY(cudaMemcpyAsync(S->d_maps + r, &map, sizeof map, cudaMemcpyHostToDevice, S->st));
         S_TRY(cudaStreamSynchronize(S->st));   // the host copy of the map goes out of scope here
     }
     S->ds_index[id] = r;
+    S->ds_bn.push_back(bn);
     *row = r;
     return RRS_OK;
 }
@@ -400,7 +405,8 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         for (size_t i = 0; i < na && capped && used < S->work_limit; ++i) take(i, 1.0);
         // tables of this step: gen tasks, halfspace tasks, selection tasks per launch key, argmin list
         std::vector<TaskDev> gen, hd;
-        std::map<int, std::vector<TaskDev>> tc;   // K extent of the planes -> tensor-core halfspace tasks
+        // (K extent of the planes, points per tile) -> tensor-core halfspace tasks
+        std::map<std::pair<int, int>, std::vector<TaskDev>> tc;
         // selection lists per (shared-memory class, G, kernel variant, dataset row for keys by k_keys or -1);
         // each launch requests the largest shared-memory need of its list
         std::map<std::tuple<size_t, int, int, int>, std::vector<TaskDev>> pd;
@@ -430,7 +436,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                 for (int j0 = 0; j0 < R->m; j0 += 128) gen.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
                 if (use_tc) {
                     // slots of a request need not be adjacent: one task never crosses a slot
-                    auto& v = tc[D.kp];
+                    auto& v = tc[std::make_pair(D.kp, S->ds_bn[row])];
                     for (int j0 = 0; j0 < R->m; j0 += 128) v.push_back(TaskDev{slot, j0, std::min(128, R->m - j0), 0});
                 } else if (R->kind == RRS_HALFSPACE) {
                     for (int j0 = 0; j0 < R->m; j0 += hper) hd.push_back(TaskDev{slot, j0, std::min(hper, R->m - j0), 0});
@@ -463,7 +469,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         const size_t o_arg = put(arg.data(), sizeof(int32_t) * arg.size());
         std::vector<std::pair<size_t, std::tuple<size_t, int, int, int>>> o_pd;
         for (auto& kv : pd) o_pd.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
-        std::vector<std::pair<size_t, int>> o_tc;
+        std::vector<std::pair<size_t, std::pair<int, int>>> o_tc;
         for (auto& kv : tc) o_tc.push_back({put(kv.second.data(), sizeof(TaskDev) * kv.second.size()), kv.first});
         S_TRY(cudaMemcpyAsync(S->d_tab, host.data(), off, cudaMemcpyHostToDevice, S->st));
         char* T = S->d_tab;
@@ -472,9 +478,9 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
         S_TRY(launch_hd_simt((const TaskDev*)(T + o_hd), (int)hd.size(), S->max_ldx, S->d_slots, S->d_ds, S->d_U,
                              S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err, S->st));
         for (auto& to : o_tc)
-            S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), to.second, S->d_slots,
-                               S->d_ds, S->d_maps, S->d_U, S->d_yz, S->d_z64, S->d_res, nullptr, S->ctx->d_err,
-                               S->st));
+            S_TRY(launch_hd_tc((const TaskDev*)(T + to.first), (int)tc[to.second].size(), to.second.first,
+                               to.second.second, S->d_slots, S->d_ds, S->d_maps, S->d_U, S->d_yz, S->d_z64, S->d_res,
+                               nullptr, S->ctx->d_err, S->st));
         size_t extra = 0;
         for (auto& po : o_pd) {
             const auto& key = po.second;

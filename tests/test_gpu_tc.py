@@ -113,3 +113,46 @@ def test_tc_exact_ties_on_a_lattice(ctx):
     ref = oracle.rrs(X, Z, H, 200, 2, 0.6, 4)
     np.testing.assert_array_equal(g["count"], ref["count"])
     np.testing.assert_array_equal(g["depth"], ref["depth"])
+
+
+def test_tensor_core_tile_width_does_not_change_counts(ctx):
+    # planes of K extent 64 run with 256- or 128-point tiles (fixed, tuned or default); counts are exact either
+    # way, so every width gives the FP32 path's counts, and a graph captured at one width is dropped when the
+    # width changes
+    X, Z = workloads.gaussian_cloud(77, 3001, 30, 9, dtype=np.float32)
+    did = ctx.register(torch.from_numpy(X).cuda())
+    Zt = torch.from_numpy(Z).cuda()
+    _, c32, _ = ctx.depth(did, Zt, rrs.RRS_HALFSPACE, 300, 3, 0.6, 5)
+    got = {}
+    for width in (0, 128, 256, 0):
+        rrs.rrs_select_tc_tile(ctx.handle, did, width)
+        _, c, _ = ctx.depth(did, Zt, rrs.RRS_HALFSPACE, 300, 3, 0.6, 5, precision=rrs.RRS_PREC_SPLIT_BF16X3)
+        got[width] = c.cpu().numpy()
+        np.testing.assert_array_equal(got[width], c32.cpu().numpy())
+    choice = rrs.rrs_autotune(ctx.handle, did, rrs.RRS_HALFSPACE, 300, 3)
+    assert choice in (128, 256)
+    # batched with graph replay, before and after a width change
+    out = torch.zeros(Z.shape[0], dtype=torch.int64, device="cuda")
+    dep = torch.zeros(Z.shape[0], dtype=torch.float64, device="cuda")
+    req = rrs.rrs_request(dataset_id=did, Z=Zt.data_ptr(), n_queries=Z.shape[0], dtype=rrs.RRS_F32,
+                          kind=rrs.RRS_HALFSPACE, n_dirs=300, n_refinements=3, cap_shrink=0.6, seed=5,
+                          depth_out=dep.data_ptr(), count_out=out.data_ptr(), precision=rrs.RRS_PREC_SPLIT_BF16X3)
+    for width in (128, 256):
+        rrs.rrs_select_tc_tile(ctx.handle, did, width)
+        for _ in range(2):
+            out.zero_()
+            rrs.rrs_depth_batched(ctx.handle, [req], use_graph=True, stream=torch.cuda.current_stream())
+            rrs.rrs_check(ctx.handle, torch.cuda.current_stream())
+            np.testing.assert_array_equal(out.cpu().numpy(), c32.cpu().numpy())
+    rrs.rrs_select_tc_tile(ctx.handle, did, 0)
+    ctx.free(did)
+
+
+def test_tensor_core_tile_choices_by_dimension(ctx):
+    # only planes of K extent 64 (d + 2 <= 64) have two tile widths; d + 2 in (64, 128] has 128; larger d has no
+    # tensor-core path
+    for d, want in ((100, {128}), (140, {0})):
+        X, _ = workloads.gaussian_cloud(d, 500, d, 1, dtype=np.float32)
+        did = ctx.register(torch.from_numpy(X).cuda())
+        assert rrs.rrs_autotune(ctx.handle, did, rrs.RRS_HALFSPACE, 100, 2) in want
+        ctx.free(did)
