@@ -1,8 +1,9 @@
 """Multi-rank logic of bench.py on CPU (gloo, world size 2).
 
-The path shards by query with no data exchange, so N GPUs run N replicas; the
-benchmark's only cross-rank step is taking the slowest rank's time and scaling
-the work by N.  These tests run that logic on two gloo ranks.
+The path shards by query with no data exchange: every rank holds the data
+cloud and takes its own queries, so the benchmark's only cross-rank step is
+taking the slowest rank's time and summing the ranks' work.  These tests run
+that logic on two gloo ranks.
 """
 import json
 import os
@@ -81,3 +82,39 @@ def test_reference_arm_line_carries_the_contract_keys():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"].startswith("projection + asymmetric projection depth")
+
+
+SHARD_WORKER = r'''
+import os, sys, json
+sys.path.insert(0, os.environ["ROOT"])
+import numpy as np
+import torch.distributed as dist
+dist.init_process_group("gloo")
+import workloads
+rank = dist.get_rank()
+Z = workloads.c2_queries(rank, 300)
+shards = [None, None]
+dist.all_gather_object(shards, Z.tolist())
+print(json.dumps({"rank": rank, "ok": True}), flush=True)
+if rank == 0:
+    a, b = np.array(shards[0], np.float32), np.array(shards[1], np.float32)
+    assert a.shape == b.shape == (300, 10)
+    assert np.array_equal(a, workloads.c2(nq=300).Z)              # rank 0: the workload's own queries
+    assert not (a[:, None, :] == b[None, :, :]).all(axis=2).any()  # no query repeats across ranks
+    assert b.min() >= -4.0 and b.max() <= 4.0 and abs(float(b.mean())) < 0.3   # same law U[-4,4]^10
+dist.barrier()
+dist.destroy_process_group()
+'''
+
+
+def test_two_gloo_ranks_take_disjoint_query_shards():
+    port = free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, ROOT=ROOT, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", SHARD_WORKER], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err

@@ -105,6 +105,16 @@ def c2(seed: int = 2, n: int = 10_000, nq: int = 1000, kind: int = PROJECTION) -
                    kind, 1000, 20, 0.7, 0)
 
 
+def c2_queries(rank: int, nq: int = 1000) -> np.ndarray:
+    """The projection-depth workload's queries taken by rank `rank` of a multi-GPU run: rank 0 the
+    workload's own, every other rank nq fresh draws from the same law U[-4,4]^10 seeded by (2, rank), so the
+    ranks share the data cloud and no query repeats across ranks."""
+    if rank == 0:
+        return c2(nq=nq).Z
+    rng = np.random.default_rng([2, rank])
+    return np.ascontiguousarray(rng.uniform(-4.0, 4.0, size=(nq, 10)), dtype=np.float32)
+
+
 def c3(seed: int = 3, n: int = 100_000, nq: int = 10_000, d: int = 50) -> Problem:
     rng = np.random.default_rng(seed)
     A = random_spd_sqrt(rng, d)
