@@ -389,3 +389,20 @@ def test_every_selection_kernel_selects_the_same_points(ctx, kind, n, d, m):
         np.testing.assert_array_equal(ch, out[0][2], err_msg=f"choice {choice}")
     g = {"depth": out[0][0], "best": out[0][1], "choice": out[0][2], "count": None}
     assert_follow(g, X, Z, kind, k, r, 0.6, 4)
+
+
+def test_kernel_choices_reject_unknown_values(ctx):
+    X, _ = workloads.gaussian_cloud(5, 100, 4, 1, dtype=np.float32)
+    did = ctx.register(torch.from_numpy(X).cuda())
+    for bad in (3, 8, -1, 1000):
+        with pytest.raises(rrs.RRSError) as e:
+            rrs.rrs_select_kernel(ctx.handle, did, 100, 4, bad)
+        assert e.value.status == rrs.RRS_ERR_INVALID_ARG
+    for bad in (64, 512, -1):
+        with pytest.raises(rrs.RRSError) as e:
+            rrs.rrs_select_tc_tile(ctx.handle, did, bad)
+        assert e.value.status == rrs.RRS_ERR_INVALID_ARG
+    with pytest.raises(rrs.RRSError) as e:
+        rrs.rrs_select_kernel(ctx.handle, 123456, 100, 4, 2)
+    assert e.value.status == rrs.RRS_ERR_NOT_FOUND
+    ctx.free(did)

@@ -36,10 +36,12 @@ def setup():
 K, R, ALPHA = 120, 4, 0.8
 
 
-def serve(ctx, batches, max_slots=4096, precision=rrs.RRS_PREC_FP32_SIMT):
+def serve(ctx, batches, max_slots=4096, precision=rrs.RRS_PREC_FP32_SIMT, work_limit=None, steps_out=None):
     """batches: list (one per step) of lists of (dataset_id, Z, kind, seed) to submit before that step."""
     srv = rrs.rrs_server_create(ctx.handle, max_slots, -(-K // R), 100, torch.cuda.current_stream(),
                                 precision=precision)
+    if work_limit is not None:
+        rrs.rrs_server_set_work_limit(srv, work_limit)
     results, pending = [], {}
     try:
         step = 0
@@ -58,6 +60,8 @@ def serve(ctx, batches, max_slots=4096, precision=rrs.RRS_PREC_FP32_SIMT):
             assert step < 10_000
         torch.cuda.synchronize()
         rrs.rrs_check(ctx.handle, torch.cuda.current_stream())
+        if steps_out is not None:
+            steps_out.append(step)
     finally:
         rrs.rrs_server_destroy(srv)
     return results
@@ -155,3 +159,36 @@ def test_served_keys_beyond_shared_memory(setup):
             np.testing.assert_array_equal(g, alone_depth(ctx, did, Z, kind, seed))
     finally:
         ctx.free(big)
+
+
+@pytest.mark.parametrize("work_limit", [1.0, 2e5, 0.0])
+def test_work_limit_changes_the_steps_not_the_results(setup, work_limit):
+    # the work limit bounds the queries that run a round in one step (at least one query); 0 runs every
+    # admitted query at every step.  A limit of one pair runs one query per step, so every query's R rounds
+    # take a step of their own.  Results equal rrs_depth alone whatever the limit.
+    ctx, ds = setup
+    batch = []
+    for i in range(4):
+        did, P = ds[i]
+        batch.append((did, np.ascontiguousarray(P.Z[:3 + i]), i % 3, 300 + i))
+    steps = []
+    res = serve(ctx, [batch], work_limit=work_limit, steps_out=steps)
+    for (did, Z, kind, seed), got in zip(batch, res):
+        np.testing.assert_array_equal(got, alone_depth(ctx, did, Z, kind, seed))
+    total_q = sum(Z.shape[0] for _, Z, _, _ in batch)
+    if work_limit == 1.0:
+        assert steps[0] >= total_q * R
+    if work_limit == 0.0:
+        assert steps[0] <= R + 1
+
+
+def test_work_limit_rejects_bad_values(setup):
+    ctx, _ = setup
+    srv = rrs.rrs_server_create(ctx.handle, 16, 30, 100, torch.cuda.current_stream())
+    try:
+        for bad in (-1.0, float("nan"), float("inf")):
+            with pytest.raises(rrs.RRSError) as e:
+                rrs.rrs_server_set_work_limit(srv, bad)
+            assert e.value.status == rrs.RRS_ERR_INVALID_ARG
+    finally:
+        rrs.rrs_server_destroy(srv)
