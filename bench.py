@@ -14,7 +14,8 @@ bounded sample of the same workload per step).  For N > 1 (torchrun) every
 rank runs its own replica of the workload (weak scaling; the path needs no
 data exchange) and the slowest rank's time is reported.
 
-Other workloads (``--workload``, one GPU): ``c3`` halfspace depth at d = 50 on
+Other workloads (``--workload``, one GPU): ``c1`` halfspace depth at d = 2 on FP64
+data (launch-bound); ``c3`` halfspace depth at d = 50 on
 the tensor cores against the FP32 path; ``c4`` 256 datasets in one batched,
 graph-captured launch sequence; ``c5`` continuous-batching serving with p50 /
 p99 latency (``--sweep`` for a rate sweep); ``grid`` the paper's per-point
@@ -99,8 +100,9 @@ def parse():
                     help="headline: keep the shared-memory heuristic for the selection kernel's directions per CTA")
     ap.add_argument("--no-halfspace", action="store_true", help="skip the secondary d=50 halfspace measurement")
     ap.add_argument("--nq", type=int, default=0, help="queries (default: the full workload)")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "grid", "ranks", "convergence"], default="c2",
-                    help="c2: PD+AP d=10 (the headline); c3: halfspace d=50, tensor-core vs FP32 paths; "
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "grid", "ranks", "convergence"], default="c2",
+                    help="c1: halfspace d=2, FP64 data (launch-bound); c2: PD+AP d=10 (the headline); "
+                         "c3: halfspace d=50, tensor-core vs FP32 paths; "
                          "c4: 256 datasets batched in one graph-captured launch sequence; c5: serving; "
                          "grid: the paper's projection-depth timing grid (its Tables 1 and 2); "
                          "ranks: its center-outward ranking correlations (Tables 4 and 5); "
@@ -236,6 +238,26 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
+    if args.workload == "c1":
+        P = workloads.c1()
+        threads = oracle.max_threads()
+        times = []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.rrs(P.X, P.Z, workloads.HALFSPACE, P.k, P.r, P.alpha, P.seed, nthreads=threads)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        value = P.Z.shape[0] * len(times) / sum(times)
+        sample = f"all {P.Z.shape[0]} queries of the d=2 halfspace workload, OpenMP over queries on {threads} host threads"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "query-depths/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD_C1, "step": sample},
+                "cpu_baseline": {"value": value, "unit": "query-depths/s", "cores": threads, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "query-depths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "c3":
         P = workloads.c3(nq=args.nq or 8)
         threads = oracle.max_threads()
@@ -469,6 +491,57 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+WORKLOAD_C1 = ("halfspace depth, d=2, n=1000 N(0,I) rows, 100 queries N(0,1.5^2 I), k=1000 dirs over r=10 rounds, "
+               "alpha=0.5, FP64 data")
+
+
+def run_c1(args):
+    """Halfspace depth at d=2 on FP64 data: 100 queries of 1,000 directions over 10 rounds, through rrs_depth
+    (FP32 path with the exact FP64 re-check).  The whole call is a few small launches per round, so it is
+    launch-bound and no roofline is claimed; the line reports the call's time and its launches."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_2506_08262_gb300 as rrs
+    dev = torch.device("cuda", 0)
+    P = workloads.c1()
+    ctx = rrs.rrs_create(0, 0)
+    did = rrs.rrs_register_dataset(ctx, torch.from_numpy(P.X).to(dev), P.X.shape[0], 2, rrs.RRS_F64, True)
+    Zd = torch.from_numpy(P.Z).to(dev)
+    nq = P.Z.shape[0]
+    dep = torch.empty(nq, dtype=torch.float64, device=dev)
+    cnt = torch.empty(nq, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rrs.rrs_depth(ctx, did, Zd, nq, rrs.RRS_F64, True, rrs.RRS_HALFSPACE, P.k, P.r, P.alpha, P.seed,
+                      rrs.RRS_PREC_FP32_SIMT, dep, cnt, None, None, True, stream)
+    for _ in range(max(3, args.warmup)):
+        step()
+    rrs.rrs_check(ctx, stream)
+    torch.cuda.synchronize()
+    launches0 = rrs.rrs_launch_count(ctx)
+    evs = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    launches = (rrs.rrs_launch_count(ctx) - launches0) // args.steps
+    rrs.rrs_check(ctx, stream)
+    rrs.rrs_free(ctx, did)
+    rrs.rrs_destroy(ctx)
+    line = {"metric": METRIC, "value": nq / (ms / 1000), "unit": "query-depths/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 projections, f64 data and exact re-check", "data": "synthetic",
+            "config": {"workload": WORKLOAD_C1, "l2": "inputs far smaller than L2; launch-bound"},
+            "gpu_launches_per_step": int(launches), "roofline": None}
+    print(json.dumps(line), flush=True)
 
 
 WORKLOAD_C3 = ("halfspace depth, d=50, n=100000 Student-t(3) rows mapped by a random SPD square root, "
@@ -1185,6 +1258,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c1":
+        run_c1(args)
     elif args.workload == "c3":
         run_c3(args)
     elif args.workload == "c4":
