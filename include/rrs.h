@@ -104,13 +104,15 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id);
  *   depth.  Halfspace counts are exact either way: every point whose fast
  *   projection lies in the near-tie band |u'x - u'z| <= b is re-checked
  *   with an exact FP64 sign test.
- *   Projection depths take the exact median / MAD / MAD_+ of the FP32
- *   projections; while n FP32 keys per direction fit in shared memory they
- *   are held there; beyond that (n above ~55,000) they are formed once per
- *   round in device memory (up to 256 MB of scratch, taken in chunks) and
- *   every selection pass reads them back, with the same arithmetic, so results
- *   do not depend on which form ran.  n is limited to 2^31 - 64 for projection
- *   depths.
+ *   Projection depths select the points holding the median / MAD / MAD_+ of
+ *   the FP32 projections (exact order statistics of the FP32 keys, ties broken
+ *   by point index) and form the depth from FP64 projections of those points
+ *   and of z.  The keys are held in shared memory while two CTAs of two
+ *   directions fit an SM (about n <= 10,000 for d <= 12); beyond that they are
+ *   formed once per round in device memory (up to 256 MB of scratch, taken in
+ *   chunks) and every selection pass reads them back, with the same
+ *   arithmetic, so results do not depend on which form ran.  n is limited to
+ *   2^31 - 64 for projection depths.
  * Outputs (each n_queries long, or n_queries*r for round_choice_out):
  *   depth_out[q]   final depth D_min (double).                      required
  *   count_out[q]   halfspace: min(#<=, #>=) at D_min, else -1.        optional
