@@ -56,15 +56,14 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # valid only for the kernel source it was taken from: `src_sha16` is the SHA-256 prefix of those files at
 # capture time, and a mismatch (the kernel changed since) reports null.
 CAPTURED = {
-    # k_pdap2<2,12>, d = 10, n = 10,000: DRAM bytes of three 50,000-direction asymmetric-depth launches; warp
-    # instructions per element the mean of one projection-depth (2.454) and one asymmetric-depth (2.116) launch
-    # at round 11 of 20 (the headline runs both kinds on the same element counts)
+    # k_pdap2<2,12>, d = 10, n = 10,000, 50,000 directions per launch: the 40 launches of one step (both kinds,
+    # 20 rounds each): DRAM bytes and warp instructions per (point, direction) element, averaged
     "k_pdap2_c2": {"src": ("paper_2506_08262_gb300/csrc/pdap.cu", "paper_2506_08262_gb300/csrc/rrs_internal.h"),
-                   "src_sha16": "49204366b3a88fe9", "traffic": 3.923e6, "warp_instr_per_element": 2.285},
+                   "src_sha16": "c190a3de1b59fa1c", "traffic": 3.967e6, "warp_instr_per_element": 2.287},
     # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50: one launch
     "k_hd_tc_c3": {"src": ("paper_2506_08262_gb300/csrc/hd_tc.cu", "paper_2506_08262_gb300/csrc/async_sync.cuh",
                            "paper_2506_08262_gb300/csrc/rrs_device.cuh"),
-                   "src_sha16": "74a410def31f32d6", "traffic": 290.53e6},
+                   "src_sha16": "78f16dea39c9afd0", "traffic": 290.41e6},
 }
 ISSUE_PER_SM_PER_CLK = 4     # one warp instruction per clock on each of the four SM sub-partitions
 
