@@ -1,6 +1,7 @@
 // Projection depth D_P and asymmetric projection depth D_AP (Sec. 2) for a block
 // of directions: y_i = u'x_i in FP32, exact order statistics (median, MAD,
-// MAD_+) of the FP32 keys, depth in FP64 from those few values.
+// MAD_+) of the FP32 keys, whose points a second kernel (k_pdap_finish)
+// re-projects in FP64 to form the depth.
 //
 // One CTA handles G <= 4 directions of one query with the G*n keys resident in
 // shared memory, or, when n is beyond what shared memory holds, G = 2
@@ -23,6 +24,7 @@
 // keys.  No per-element work uses FP64.
 #include <cuda_runtime.h>
 #include <float.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -51,17 +53,17 @@ constexpr int FB_CAP = CAP + CAP1;  // fallback gather buffer: a direction's two
 // the named barrier 1 + g, so the directions of a CTA never wait for each other.
 struct Ctl {
     float lo_b[MAXG], sc_y[MAXG];      // bucket map of the keys: about (y - lo_b) * sc_y
-    float off_y[MAXG];                 // -lo_b * sc_y (bucket_fma offset)
+    float off_y[MAXG];                 // -lo_b * sc_y + 2^23 (bucket_m offset)
     float scale[MAXG];                 // sigma_u (or the radius) of each direction
     int red[MAXG][NWARP];
     float fred[MAXG][2 * NWARP];
     int fill[MAXG][2];
     int f_b1[MAXG], f_c1[MAXG], f_b2[MAXG], f_c2[MAXG];   // bucket search results
+    int fr_b[MAXG][4], fr_c[MAXG][4], fr_h[MAXG][4];      // gfindn: bucket, keys below, keys in it
     float pv1[MAXG], pv2[MAXG];                           // rank pick results
     int pi1[MAXG], pi2[MAXG];                             // their point indices
     int gn[MAXG];
     int gi[MAXG];                                         // smallest index of a tied run (fallback)
-    double y64[MAXG][4];                                  // FP64 projections of the selected points
 };
 
 template <int GS>
@@ -91,6 +93,31 @@ __device__ __forceinline__ int bucket_fma(float y, float sc, float off)
 {
     const unsigned b = __float2uint_rz(__fmaf_rn(y, sc, off));
     return b < (unsigned)(NBK - 1) ? (int)b : NBK - 1;
+}
+
+// Bucket maps of k_pdap2: y*sc + off rounded once to an integer by the FMA itself.  o23 is off + 2^23,
+// so a result r in [2^23, 2^24) is an integer and its float bits are MAGIC + (r - 2^23).  bucket_raw
+// returns those bits as an int: non-decreasing in y for every result that is not a negative float, and
+// every negative float is a negative int.  bucket_m clamps them to [0, NBK): no float-to-integer
+// conversion, monotone non-decreasing in y.  A run of buckets [b1, b2] is the set of raw values in
+// [raw_lo(b1), raw_hi(b2)] (signed comparisons), the edge buckets taking every value clamped into them.
+constexpr int MAGIC = 0x4B000000;   // float bits of 2^23
+constexpr float TWO23 = 8388608.0f;
+__device__ __forceinline__ int bucket_raw(float y, float sc, float o23) { return __float_as_int(__fmaf_rn(y, sc, o23)); }
+template <int NBK = NB>
+__device__ __forceinline__ int bucket_m(float y, float sc, float o23)
+{
+    return min(max(bucket_raw(y, sc, o23), MAGIC), MAGIC + NBK - 1) - MAGIC;
+}
+template <int NBK = NB>
+__device__ __forceinline__ int raw_lo(int b)
+{
+    return b <= 0 ? INT_MIN : MAGIC + b;
+}
+template <int NBK = NB>
+__device__ __forceinline__ int raw_hi(int b)
+{
+    return b >= NBK - 1 ? INT_MAX : MAGIC + b;
 }
 
 __device__ __forceinline__ float warp_max(float v)
@@ -142,6 +169,38 @@ __device__ void gminmax(const Grp<GS>& q, float lo, float hi, CT& C, float& olo,
     q.sync();
 }
 
+// Group min and max of two pairs at once (one barrier round for both).
+template <int GS, class CT>
+__device__ void gminmax2(const Grp<GS>& q, float& lo1, float& hi1, float& lo2, float& hi2, CT& C)
+{
+    constexpr int NW = GS / 32;   // at most 16: 4 NW values fit the 2 NWARP cells of fred
+    static_assert(4 * NW <= 2 * NWARP, "gminmax2 scratch");
+    lo1 = warp_min(lo1);
+    hi1 = warp_max(hi1);
+    lo2 = warp_min(lo2);
+    hi2 = warp_max(hi2);
+    const int w = q.t >> 5;
+    if ((q.t & 31) == 0) {
+        C.fred[q.g][w] = lo1;
+        C.fred[q.g][NW + w] = hi1;
+        C.fred[q.g][2 * NW + w] = lo2;
+        C.fred[q.g][3 * NW + w] = hi2;
+    }
+    q.sync();
+    lo1 = C.fred[q.g][0];
+    hi1 = C.fred[q.g][NW];
+    lo2 = C.fred[q.g][2 * NW];
+    hi2 = C.fred[q.g][3 * NW];
+#pragma unroll
+    for (int i = 1; i < NW; ++i) {
+        lo1 = fminf(lo1, C.fred[q.g][i]);
+        hi1 = fmaxf(hi1, C.fred[q.g][NW + i]);
+        lo2 = fminf(lo2, C.fred[q.g][2 * NW + i]);
+        hi2 = fmaxf(hi2, C.fred[q.g][3 * NW + i]);
+    }
+    q.sync();
+}
+
 // Exclusive scan of h[0..NB) by the group; the bucket holding rank ra and the
 // one holding rank rb (ra <= rb, both below the total), with the keys below each.
 template <int GS, class CT, int NBK = NB>
@@ -171,7 +230,8 @@ __device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, CT& C
     if (lane == 31) C.red[q.g][w] = incl;
     q.sync();
     int base = 0;
-    for (int i = 0; i < w; ++i) base += C.red[q.g][i];
+#pragma unroll
+    for (int i = 0; i < GS / 32; ++i) base += i < w ? C.red[q.g][i] : 0;
     int c = base + incl - own;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -196,6 +256,68 @@ __device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, CT& C
     q.sync();
 }
 
+// One scan of h[0..NB) by the group locating the buckets of NR ranks rk[] (each below the total): for
+// each, the bucket, the keys below it and the keys in it.  With PREFIX, h becomes its inclusive prefix
+// counts in the same pass.
+template <int GS, int NR, bool PREFIX>
+__device__ void gfindn(const Grp<GS>& q, unsigned* h, const int (&rk)[NR], Ctl& C, int (&bo)[NR], int (&co)[NR],
+                       int (&ho)[NR])
+{
+    constexpr int PER = NB / GS;
+    const int lane = q.t & 31, w = q.t >> 5;
+    int own = 0;
+    unsigned v[PER];
+    uint4* h4 = reinterpret_cast<uint4*>(h + q.t * PER);
+#pragma unroll
+    for (int k = 0; k < PER / 4; ++k) {
+        const uint4 a = h4[k];
+        v[4 * k] = a.x;
+        v[4 * k + 1] = a.y;
+        v[4 * k + 2] = a.z;
+        v[4 * k + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) own += (int)v[k];
+    int incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) C.red[q.g][w] = incl;
+    q.sync();
+    int base = 0;
+#pragma unroll
+    for (int i = 0; i < GS / 32; ++i) base += i < w ? C.red[q.g][i] : 0;
+    int c = base + incl - own;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int hk = (int)v[k];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (c <= rk[j] && rk[j] < c + hk) {
+                C.fr_b[q.g][j] = q.t * PER + k;
+                C.fr_c[q.g][j] = c;
+                C.fr_h[q.g][j] = hk;
+            }
+        }
+        c += hk;
+        if (PREFIX) v[k] = (unsigned)c;
+    }
+    if (PREFIX) {
+#pragma unroll
+        for (int k = 0; k < PER / 4; ++k) h4[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    q.sync();
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        bo[j] = C.fr_b[q.g][j];
+        co[j] = C.fr_c[q.g][j];
+        ho[j] = C.fr_h[q.g][j];
+    }
+    q.sync();
+}
+
 // Values and point indices of the 0-based ranks s1 <= s2 among the pairs (buf, ib)[0..cnt), ordered by
 // value and then by point index, by the group.  The indices of one buffer are distinct, so every rank
 // names one pair and the choice among equal values never depends on the gather order.
@@ -203,21 +325,36 @@ template <int GS, class CT>
 __device__ void gpick(const Grp<GS>& q, const float* buf, const int* ib, int cnt, int s1, int s2, CT& C, float& o1,
                       float& o2, int& i1, int& i2)
 {
-    for (int t = q.t; t < cnt; t += GS) {
-        const float v = buf[t];
-        const int iv = ib[t];
+    // tpk adjacent threads (one warp) rank one pair, each against every tpk-th pair, and add their counts:
+    // small sets are ranked in about cnt / tpk dependent steps.  Every thread of the group runs the same
+    // number of outer iterations, so the shuffles see whole warps.
+    const int tpk = cnt * 8 <= GS ? 8 : (cnt * 4 <= GS ? 4 : (cnt * 2 <= GS ? 2 : 1));
+    const int sub = q.t & (tpk - 1);
+    for (int t0 = 0; t0 < cnt; t0 += GS / tpk) {
+        const int t = t0 + q.t / tpk;
+        const bool live = t < cnt;
         int r = 0;
-        for (int s = 0; s < cnt; ++s) {
-            const float w2 = buf[s];
-            r += (w2 < v) | ((w2 == v) & (ib[s] < iv));
+        float v = 0.f;
+        int iv = 0;
+        if (live) {
+            v = buf[t];
+            iv = ib[t];
+#pragma unroll 4
+            for (int s = sub; s < cnt; s += tpk) {
+                const float w2 = buf[s];
+                r += (w2 < v) | ((w2 == v) & (ib[s] < iv));
+            }
         }
-        if (r == s1) {
-            C.pv1[q.g] = v;
-            C.pi1[q.g] = iv;
-        }
-        if (r == s2) {
-            C.pv2[q.g] = v;
-            C.pi2[q.g] = iv;
+        for (int o = 1; o < tpk; o <<= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+        if (live && sub == 0) {
+            if (r == s1) {
+                C.pv1[q.g] = v;
+                C.pi1[q.g] = iv;
+            }
+            if (r == s2) {
+                C.pv2[q.g] = v;
+                C.pi2[q.g] = iv;
+            }
         }
     }
     q.sync();
@@ -303,41 +440,6 @@ __device__ void gpick_wide(const Grp<GS>& q, const float* buf, const int* ib, in
     }
     q.sync();
     gpick(q, tb, ti, n2, s1 - c1, s2 - c1, C, o1, o2, i1, i2);
-}
-
-// Inclusive prefix sums of h[0..NB) in place, by the group.
-template <int GS, class CT>
-__device__ void gprefix(const Grp<GS>& q, unsigned* h, CT& C)
-{
-    constexpr int PER = NB / GS;
-    const int lane = q.t & 31, w = q.t >> 5;
-    unsigned v[PER];
-    uint4* h4 = reinterpret_cast<uint4*>(h + q.t * PER);
-#pragma unroll
-    for (int k = 0; k < PER / 4; ++k) {
-        const uint4 a = h4[k];
-        v[4 * k] = a.x;
-        v[4 * k + 1] = a.y;
-        v[4 * k + 2] = a.z;
-        v[4 * k + 3] = a.w;
-    }
-#pragma unroll
-    for (int k = 1; k < PER; ++k) v[k] += v[k - 1];
-    int incl = (int)v[PER - 1];
-    const int own = incl;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) C.red[q.g][w] = incl;
-    q.sync();
-    int base = incl - own;
-    for (int i = 0; i < w; ++i) base += C.red[q.g][i];
-#pragma unroll
-    for (int k = 0; k < PER / 4; ++k)
-        h4[k] = make_uint4(v[4 * k] + base, v[4 * k + 1] + base, v[4 * k + 2] + base, v[4 * k + 3] + base);
-    q.sync();
 }
 
 // Generic exact selection of ranks q1 <= q2 over one direction's values f(0..L-1),
@@ -500,27 +602,27 @@ struct KeysRecomputed {
 // [ba - s, bb + s]; the MAD ranks then deviate from the median by more than (ss - 2) and less than
 // (ss + w) bucket widths, so their keys lie in two runs L, R at bucket distance about ss on either side.
 // The runs taken here add two buckets on each side of that band, which lets the bound check of
-// mad_from_runs pass; they are symmetric about (ba + bb) / 2, i.e. the buckets b with
-// |2b - (ba + bb)| in [dl2, dl2 + dw2].  H becomes prefix counts.  The runs stay unset (dl2 untouched)
-// when they would overlap the median run or the edge buckets, or hold more than cap keys.
+// mad_from_runs pass; they are symmetric about (ba + bb) / 2: L = [L0, L1] below the median run and
+// R = [R0, R1] above it.  H holds inclusive prefix counts (gfindn with PREFIX).  The runs stay unset (r untouched) when they would
+// overlap the median run or the edge buckets, or hold more than cap keys.
 template <int GS, class CT>
-__device__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, int k2, int cap, int& c2, int& dl2,
-                         int& dw2, int& cnt1, int& c_in)
+__device__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, int k2, int cap, int4& r,
+                         int& cnt1, int& c_in)
 {
-    gprefix(q, H, C);
     if (q.t == 0) C.f_b1[q.g] = NB;
     q.sync();
+    // the window count is non-decreasing in s: each thread tests its PER values of s with independent
+    // loads and offers the first that exceeds k2
     constexpr int PER = NB / GS;
-#pragma unroll 1
-    for (int k = 0; k < PER; ++k) {
+    int first = NB;
+#pragma unroll
+    for (int k = PER - 1; k >= 0; --k) {
         const int s = q.t * PER + k;
         const int hi = bb + s < NB - 1 ? bb + s : NB - 1, lo = ba - s;
         const int c = (int)H[hi] - (lo >= 1 ? (int)H[lo - 1] : 0);
-        if (c > k2) {
-            atomicMin(&C.f_b1[q.g], s);
-            break;
-        }
+        if (c > k2) first = s;
     }
+    if (first < NB) atomicMin(&C.f_b1[q.g], first);
     q.sync();
     const int ss = C.f_b1[q.g];
     q.sync();
@@ -531,9 +633,7 @@ __device__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, i
         if (cl <= cap) {
             cnt1 = cl;
             c_in = (int)(H[R0 - 1] - H[L1]);
-            c2 = ba + bb;
-            dl2 = 2 * ss - w - 7;
-            dw2 = 4 * w + 10;
+            r = make_int4(L0, L1, R0, R1);
         }
     }
 }
@@ -560,9 +660,8 @@ __device__ bool mad_from_runs(const Grp<GS>& q, float* B1, int* I1, int cnt1, in
         }
         B1[t] = fabsf(__fsub_rn(v, m));
     }
-    float la, lb, ra, rb;
-    gminmax(q, lmin, lmax, C, la, lb);
-    gminmax(q, rmin, rmax, C, ra, rb);
+    gminmax2(q, lmin, lmax, rmin, rmax, C);
+    const float la = lmin, lb = lmax, ra = rmin, rb = rmax;
     if (!(lb > -FLT_MAX && ra < FLT_MAX && s1 >= 0 && s2 < cnt1)) return false;
     const float inner = fmaxf(__fsub_rn(m, lb), __fsub_rn(ra, m));
     const float outer = fminf(__fsub_rn(m, la), __fsub_rn(rb, m));
@@ -588,18 +687,91 @@ __device__ __forceinline__ double proj64(const DsDev& D, const float* u, int i)
     return acc;
 }
 
-// Exact median / MAD / MAD_+ of one direction's keys y (after the projection pass) and the
-// depth, by its group q of GS threads.  The selection runs on the FP32 keys and yields the points
-// holding the wanted order statistics (ties broken by point index); the depth is then formed from
-// FP64 projections of those few points and the FP64 y_z (yzv).
+// The points a selection kernel picked for one direction are written into the direction's result cell in
+// place of its depth, which k_pdap_finish then forms from them: the points of the median ranks (im1, im2)
+// and of the MAD or MAD_+ ranks (ip1, ip2); -1 where a selection failed (its error flag is set), and
+// ip1 = ip2 = NOPOS for D_AP when no key lies above the median (MAD_+ = 0).  Two 8-byte stores: a result
+// cell is 8-byte aligned.
+constexpr int NOPOS = -2;
+__device__ __forceinline__ void put_picks(ResDev* cell, int im1, int im2, int ip1, int ip2)
+{
+    int2* c = reinterpret_cast<int2*>(cell);
+    c[0] = make_int2(im1, im2);
+    c[1] = make_int2(ip1, ip2);
+}
+
+// FP64 finish of a selection launch: the depth of every direction from its picks (put_picks).  Four
+// threads per direction, one per picked point, each forming the point's FP64 projection (proj64: one
+// sequential FMA chain over the dims, the order in which the direction generator forms y_z, so a query
+// equal to a data point projects to the same value); the first of the four forms
+//   D_P  = 1 / (1 + |y_z - med| / MAD),   D_AP = 1 / (1 + (y_z - med)_+ / MAD_+)      (Sec. 2)
+// with med the mean of the two median points (even n: the mean of the middle pair, odd n: the point
+// twice), and writes it over the picks.  A kernel of its own: with thousands of directions in flight the
+// long FP64 latencies overlap, where inside a selection CTA they would hold up the whole group.
+__global__ void __launch_bounds__(256) k_pdap_finish(const TaskDev* __restrict__ tasks, int ntasks, int group,
+                                                     const SlotDev* __restrict__ slots,
+                                                     const DsDev* __restrict__ dsets, const float* __restrict__ U,
+                                                     const double* __restrict__ yz, ResDev* __restrict__ res)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = (int)(t & 3);
+    const int64_t dir = t >> 2;
+    const int64_t ti = dir / group;
+    const int g = (int)(dir - ti * group);
+    bool live = ti < ntasks;
+    TaskDev T{};
+    if (live) {
+        T = tasks[ti];
+        live = g < T.nj;
+    }
+    double y = 0.0;
+    int2 a = make_int2(-1, -1), b = make_int2(-1, -1);
+    bool ap = false;
+    double yzv = 0.0;
+    ResDev* cell = nullptr;
+    if (live) {
+        const SlotDev& S = slots[T.slot];
+        const DsDev& D = dsets[S.ds];
+        cell = res + S.roff + T.j0 + g;
+        a = reinterpret_cast<const int2*>(cell)[0];
+        b = reinterpret_cast<const int2*>(cell)[1];
+        ap = S.kind == 2;
+        yzv = yz[S.roff + T.j0 + g];
+        const int sel = k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? b.x : b.y));
+        if (sel >= 0) y = proj64(D, U + S.uoff + (int64_t)(T.j0 + g) * D.ldx, sel);
+    }
+    // every lane of the warp takes part in the shuffles; the four lanes of a direction are adjacent
+    const int lane = threadIdx.x & 31, l0 = lane & ~3;
+    const double y0 = __shfl_sync(0xFFFFFFFFu, y, l0), y1 = __shfl_sync(0xFFFFFFFFu, y, l0 + 1);
+    const double y2 = __shfl_sync(0xFFFFFFFFu, y, l0 + 2), y3 = __shfl_sync(0xFFFFFFFFu, y, l0 + 3);
+    if (!live || k != 0) return;
+    const int im1 = a.x, im2 = a.y, ip1 = b.x, ip2 = b.y;
+    double depth = __longlong_as_double(0x7FF8000000000000LL);   // a failed selection (error flag set)
+    if (im1 >= 0 && im2 >= 0) {
+        const double med = (y0 + y1) * 0.5;
+        if (ap) {
+            double madp = 0.0;
+            if (ip1 != NOPOS) madp = ip1 >= 0 && ip2 >= 0 ? fmax(((y2 - med) + (y3 - med)) * 0.5, 0.0) : depth;
+            depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
+        } else if (ip1 >= 0 && ip2 >= 0) {
+            depth = depth_from(fabs(yzv - med), (fabs(y2 - med) + fabs(y3 - med)) * 0.5);
+        }
+    }
+    *cell = ResDev{depth, -1};
+}
+
+// Exact median / MAD / MAD_+ of one direction's keys y (after the projection pass), by its group q of
+// GS threads.  The selection runs on the FP32 keys and yields the points holding the wanted order
+// statistics (ties broken by point index), written to the direction's result cell (put_picks);
+// k_pdap_finish forms the depth from FP64 projections of those few points and the FP64 y_z.
 //   median  the bucket run of ranks k1, k2 (from the key histogram H) is gathered and ranked;
 //   D_P     a |y - med| histogram pass, then the gather and ranking of the MAD run;
 //   D_AP    in the median's gather pass, the run of the MAD_+ ranks guessed for no key tying the median.
 // Runs that overflow the gather buffer fall back to iterated bucket selection.
 template <int GS, class K>
 __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C, unsigned* H, float* B0, int* I0,
-                                           int n, bool ap, const float* u, const DsDev& D, double yzv, int64_t roff,
-                                           ResDev* __restrict__ res, int* err)
+                                           int n, bool ap, const DsDev& D, int64_t roff, ResDev* __restrict__ res,
+                                           int* err)
 {
     const int g = q.g;
     float* B1 = B0 + CAP;   // CAP1 entries: MAD_+ guess run (D_AP) or the runs L, R / the MAD run (D_P)
@@ -610,44 +782,60 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
     const float qnan = __int_as_float(0x7FC00000);
     constexpr int OFF = 1 << 30;   // a run start no bucket test can reach
 
-    int ba, ca, bb, cb;
-    gfind(q, H, k1, k2, C, ba, ca, bb, cb);
-    const int c_lo0 = ca, cnt0 = cb + (int)H[bb] - ca;
-    int fb = cnt0 > CAP ? 1 : 0;   // 1: fall back for every statistic, 2: only for the spread
-    // second gathered set: buckets b with |2b - c2| in [dl2, dl2 + dw2]
-    int c2 = 0, dl2 = OFF, dw2 = 0, c_lo1 = 0, cnt1 = 0, c_in = 0;
+    // one histogram scan: the median ranks, and for D_AP the ranks of the MAD_+ run guessed for no key
+    // tying the median (for D_P the scan leaves prefix counts for mad_runs)
     const int npos_guess = (n & 1) ? (n - 1) / 2 : n / 2;
-    if (ap && npos_guess > 0) {
-        const int base = n - npos_guess;
-        int b3, c3, b4, c4;
-        gfind(q, H, base + (npos_guess - 1) / 2, base + npos_guess / 2, C, b3, c3, b4, c4);
-        c_lo1 = c3;
-        cnt1 = c4 + (int)H[b4] - c3;
-        if (cnt1 > CAP1) fb = 1;
-        c2 = 2 * b3 + (b4 - b3);   // the run [b3, b4]
-        dl2 = 0;
-        dw2 = b4 - b3;
-    } else if (!ap && !fb) {
-        mad_runs(q, H, C, ba, bb, k2, CAP1, c2, dl2, dw2, cnt1, c_in);
+    int ba, ca, bb, cb, hb;
+    int b3 = 0, c3 = 0, b4 = 0, c4 = 0, h4 = 0;
+    if (ap) {
+        const int gb = n - npos_guess;
+        const int rk[4] = {k1, k2, npos_guess > 0 ? gb + (npos_guess - 1) / 2 : k1,
+                           npos_guess > 0 ? gb + npos_guess / 2 : k2};
+        int bo[4], co[4], ho[4];
+        gfindn<GS, 4, false>(q, H, rk, C, bo, co, ho);
+        ba = bo[0], ca = co[0], bb = bo[1], cb = co[1], hb = ho[1];
+        b3 = bo[2], c3 = co[2], b4 = bo[3], c4 = co[3], h4 = ho[3];
+    } else {
+        const int rk[2] = {k1, k2};
+        int bo[2], co[2], ho[2];
+        gfindn<GS, 2, true>(q, H, rk, C, bo, co, ho);
+        ba = bo[0], ca = co[0], bb = bo[1], cb = co[1], hb = ho[1];
     }
+    const int c_lo0 = ca, cnt0 = cb + hb - ca;
+    int fb = cnt0 > CAP ? 1 : 0;   // 1: fall back for every statistic, 2: only for the spread
+    // second gathered set: the buckets of one or two runs [r.x, r.y], [r.z, r.w] (x > y: no run)
+    int4 r2 = make_int4(OFF, -OFF, OFF, -OFF);
+    int c_lo1 = 0, cnt1 = 0, c_in = 0;
+    if (ap && npos_guess > 0) {
+        c_lo1 = c3;
+        cnt1 = c4 + h4 - c3;
+        if (cnt1 > CAP1) fb = 1;
+        r2 = make_int4(b3, b4, OFF, -OFF);   // the run [b3, b4]
+    } else if (!ap && !fb) {
+        mad_runs(q, H, C, ba, bb, k2, CAP1, r2, cnt1, c_in);
+    }
+    const bool second = r2.x <= r2.y;
     float m1 = qnan, m2 = qnan, p1 = 0.f, p2 = 0.f;
     int im1 = -1, im2 = -1, ip1 = -1, ip2 = -1;
     int npos = 0;
     if (!fb) {
         if (q.t < 2) C.fill[g][q.t] = 0;
         q.sync();
-        const int bl0 = ba, bw0 = bb - ba;
-        const bool second = dl2 != OFF;
+        // the runs as ranges of raw bucket values (signed compares; the edge buckets take every value
+        // clamped into them)
+        const int ml = raw_lo(ba), mh = raw_hi(bb);
+        const int xl1 = second ? raw_lo(r2.x) : INT_MAX, xh1 = second ? raw_hi(r2.y) : INT_MIN;
+        const int xl2 = r2.z <= r2.w ? raw_lo(r2.z) : INT_MAX, xh2 = r2.z <= r2.w ? raw_hi(r2.w) : INT_MIN;
         auto gather = [&](float v, int i) {
-            const int b = bucket_fma(v, sc, of);
-            if ((unsigned)(b - bl0) <= (unsigned)bw0) {
+            const int rv = bucket_raw(v, sc, of);
+            if (rv >= ml && rv <= mh) {
                 const int pos = atomicAdd(&C.fill[g][0], 1);
                 if (pos < CAP) {
                     B0[pos] = v;
                     I0[pos] = i;
                 }
             }
-            if (second && (unsigned)(abs(2 * b - c2) - dl2) <= (unsigned)dw2) {
+            if ((rv >= xl1 && rv <= xh1) || (rv >= xl2 && rv <= xh2)) {
                 const int pos = atomicAdd(&C.fill[g][1], 1);
                 if (pos < CAP1) {
                     B1[pos] = v;
@@ -680,7 +868,7 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
             }
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
-            if (!(dl2 != OFF && mad_from_runs<GS, CAP>(q, B1, I1, cnt1, k1 - c_in, k2 - c_in, m, H, B0, I0, C, p1,
+            if (!(second && mad_from_runs<GS, CAP>(q, B1, I1, cnt1, k1 - c_in, k2 - c_in, m, H, B0, I0, C, p1,
                                                        p2, ip1, ip2))) {
                 // |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
                 float dmax = D.cov ? 4.0f * C.scale[g] : 0.0f;
@@ -693,13 +881,13 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
                 q.sync();
                 for (int i = 4 * q.t; i < n4; i += 4 * GS) {
                     const float4 y4 = y.get4(i);
-                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.x, m)), scd, 0.0f)], 1u);
-                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.y, m)), scd, 0.0f)], 1u);
-                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.z, m)), scd, 0.0f)], 1u);
-                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y4.w, m)), scd, 0.0f)], 1u);
+                    atomicAdd(&H[bucket_m(fabsf(__fsub_rn(y4.x, m)), scd, TWO23)], 1u);
+                    atomicAdd(&H[bucket_m(fabsf(__fsub_rn(y4.y, m)), scd, TWO23)], 1u);
+                    atomicAdd(&H[bucket_m(fabsf(__fsub_rn(y4.z, m)), scd, TWO23)], 1u);
+                    atomicAdd(&H[bucket_m(fabsf(__fsub_rn(y4.w, m)), scd, TWO23)], 1u);
                 }
                 for (int i = n4 + q.t; i < n; i += GS)
-                    atomicAdd(&H[bucket_fma(fabsf(__fsub_rn(y.get(i), m)), scd, 0.0f)], 1u);
+                    atomicAdd(&H[bucket_m(fabsf(__fsub_rn(y.get(i), m)), scd, TWO23)], 1u);
                 q.sync();
                 int da, dca, db, dcb;
                 gfind(q, H, k1, k2, C, da, dca, db, dcb);
@@ -712,7 +900,7 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
                     const int bwd = db - da;
                     auto gd = [&](float v, int i) {
                         const float dv = fabsf(__fsub_rn(v, m));
-                        const int b = bucket_fma(dv, scd, 0.0f);
+                        const int b = bucket_m(dv, scd, TWO23);
                         if ((unsigned)(b - da) <= (unsigned)bwd) {
                             const int pos = atomicAdd(&C.fill[g][1], 1);
                             if (pos < CAP1) {
@@ -767,25 +955,8 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
         }
     }
 
-    // ---- depth from FP64 projections of the selected points --------------------------------
-    const int sel = q.t == 0 ? im1 : (q.t == 1 ? im2 : (q.t == 2 ? ip1 : ip2));
-    if (q.t < 4) C.y64[g][q.t] = sel >= 0 ? proj64(D, u, sel) : 0.0;
-    q.sync();
-    if (q.t == 0) {
-        const double* Y = C.y64[g];
-        double depth = __longlong_as_double(0x7FF8000000000000LL);   // a failed selection (error flag set)
-        if (im1 >= 0 && im2 >= 0) {
-            const double med = (Y[0] + Y[1]) * 0.5;
-            if (ap) {
-                double madp = 0.0;
-                if (npos > 0) madp = ip1 >= 0 && ip2 >= 0 ? fmax(((Y[2] - med) + (Y[3] - med)) * 0.5, 0.0) : depth;
-                depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
-            } else if (ip1 >= 0 && ip2 >= 0) {
-                depth = depth_from(fabs(yzv - med), (fabs(Y[2] - med) + fabs(Y[3] - med)) * 0.5);
-            }
-        }
-        res[roff + g] = ResDev{depth, -1};
-    }
+    // ---- the picks, for the FP64 finish (k_pdap_finish) ---------------------------------------
+    if (q.t == 0) put_picks(res + roff + g, im1, im2, ap && npos == 0 ? NOPOS : ip1, ap && npos == 0 ? NOPOS : ip2);
 }
 
 // Every live direction of the CTA: group g of cta_threads<G>() / G threads handles direction g alone,
@@ -794,8 +965,7 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
 template <int G, int DP4, bool STREAM>
 __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const float* uS, unsigned* hist, float* buf,
                                             int* ibuf, int n, int npad, bool ap, const DsDev& D, int GA,
-                                            const double* yz, int64_t roff, ResDev* __restrict__ res, int* err,
-                                            const float* kin)
+                                            int64_t roff, ResDev* __restrict__ res, int* err, const float* kin)
 {
     constexpr int GS = cta_threads<G>() / G;   // threads per direction group
     const int tid = threadIdx.x;
@@ -806,16 +976,15 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
     float* B0 = buf + (size_t)g * (CAP + CAP1);   // two gather runs, contiguous (FB_CAP for the fallback)
     int* I0 = ibuf + (size_t)g * (CAP + CAP1);    // the point index of every gathered key
     const float* u = uS + (size_t)g * D.ldx;
-    const double yzv = yz[roff + g];
     if (STREAM && kin) {
         const KeysArray y{kin + ((size_t)blockIdx.x * G + g) * npad};
-        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, D, roff, res, err);
     } else if (STREAM) {
         const KeysRecomputed<DP4> y{D.X32, u, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
-        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, D, roff, res, err);
     } else {
         const KeysArray y{keys + (size_t)g * npad};
-        select_dir<GS>(q, y, C, H, B0, I0, n, ap, u, D, yzv, roff, res, err);
+        select_dir<GS>(q, y, C, H, B0, I0, n, ap, D, roff, res, err);
     }
 }
 
@@ -827,8 +996,7 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
 template <int G, int DP4, bool STREAM>
 __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                 const double* __restrict__ yz, ResDev* __restrict__ res, int* err,
-                                                 const float* __restrict__ kin)
+                                                 ResDev* __restrict__ res, int* err, const float* __restrict__ kin)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ Ctl C;
@@ -849,22 +1017,25 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     constexpr int NTK = cta_threads<G>();
     for (int e = tid; e < G * ldx; e += NTK) uS[e] = (e / ldx < GA) ? U[S.uoff + (int64_t)T.j0 * ldx + e] : 0.0f;
     for (int e = tid; e < G * NB / 4; e += NTK) reinterpret_cast<uint4*>(hist)[e] = make_uint4(0u, 0u, 0u, 0u);
-    __syncthreads();
     // per-direction bucket range: the centre's projection +- 5 sigma_u (sigma_u^2 = u' Cov u),
     // or +- the radius about the centre when no covariance is kept.  Keys outside the range go
     // to the edge buckets, which keeps the bucket map monotone.  One warp per direction: lanes
     // take rows of Cov (the range is a heuristic, so its summation order is free); y_z keeps the
     // keys' own arithmetic (one lane, sequential FMAs).
+    // The range warps read their direction from U itself (the values the CTA stages in uS), so the range
+    // is formed while the staging goes on, before the one barrier.
     if ((tid >> 5) < G) {
         const int g = tid >> 5, lane = tid & 31;
-        const float* u = uS + g * ldx;
         float yc = 0.0f, qf = 0.0f;
-        for (int r = lane; r < d; r += 32) yc = fmaf(u[r], D.center[r], yc);
-        if (D.cov) {
-            // lanes stride over the d x d entries, so the covariance loads are independent of each other
-            for (int e = lane; e < d * d; e += 32) {
-                const int r = e / d, c2 = e - r * d;
-                qf = fmaf(D.cov[e], __fmul_rn(u[r], u[c2]), qf);
+        if (g < GA) {   // inert directions keep a zero direction, as staged
+            const float* u = U + S.uoff + (int64_t)(T.j0 + g) * ldx;
+            for (int r = lane; r < d; r += 32) yc = fmaf(u[r], D.center[r], yc);
+            if (D.cov) {
+                // lanes stride over the d x d entries, so the covariance loads are independent of each other
+                for (int e = lane; e < d * d; e += 32) {
+                    const int r = e / d, c2 = e - r * d;
+                    qf = fmaf(D.cov[e], __fmul_rn(u[r], u[c2]), qf);
+                }
             }
         }
 #pragma unroll
@@ -884,7 +1055,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
             if (!(half > 0.0f)) half = fmaxf(fabsf(yc), 1.0f);
             C.lo_b[g] = yc - half;
             C.sc_y[g] = __fdiv_rn((float)NB, __fadd_rn(half, half));
-            C.off_y[g] = __fmul_rn(-C.lo_b[g], C.sc_y[g]);
+            C.off_y[g] = __fadd_rn(__fmul_rn(-C.lo_b[g], C.sc_y[g]), TWO23);
         }
     }
     __syncthreads();
@@ -901,7 +1072,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (!STREAM) keys[(size_t)g * npad + i] = acc[g];
-                atomicAdd(&hist[g * NB + bucket_fma(acc[g], sc[g], of[g])], 1u);
+                atomicAdd(&hist[g * NB + bucket_m(acc[g], sc[g], of[g])], 1u);
             }
         };
         if (kin) {
@@ -916,7 +1087,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 for (int h = 0; h < 4; ++h) {
                     if (i + h < n) {
                         if (!STREAM) keys[(size_t)g * npad + i + h] = kv[h];
-                        atomicAdd(&hist[g * NB + bucket_fma(kv[h], sc[g], of[g])], 1u);
+                        atomicAdd(&hist[g * NB + bucket_m(kv[h], sc[g], of[g])], 1u);
                     }
                 }
             }
@@ -945,9 +1116,9 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 }
                 const float ka = key_halves<D4>(ua, xv), kb = key_halves<D4>(ub, xv);
                 if (!STREAM) keys[(size_t)(2 * pair) * npad + i] = ka;
-                atomicAdd(&hist[(2 * pair) * NB + bucket_fma(ka, sca, ofa)], 1u);
+                atomicAdd(&hist[(2 * pair) * NB + bucket_m(ka, sca, ofa)], 1u);
                 if (!STREAM) keys[(size_t)(2 * pair + 1) * npad + i] = kb;
-                atomicAdd(&hist[(2 * pair + 1) * NB + bucket_fma(kb, scb, ofb)], 1u);
+                atomicAdd(&hist[(2 * pair + 1) * NB + bucket_m(kb, scb, ofb)], 1u);
             }
         } else if (DP4 > 0) {
             float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
@@ -1016,7 +1187,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     }
     __syncthreads();
 
-    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, ibuf, n, npad, ap, D, GA, yz, S.roff + T.j0, res, err, kin);
+    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, ibuf, n, npad, ap, D, GA, S.roff + T.j0, res, err, kin);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1047,7 +1218,6 @@ struct CtlW {
     float pv1[WPC], pv2[WPC];
     int pi1[WPC], pi2[WPC];
     int gn[WPC], gi[WPC];
-    double y64[WPC][4];
     // gather-pass tests of every direction: bucket map (sc, off), median run [bl0, bl0 + bw0], second set
     // |2b - c2| in [dl2, dl2 + dw2]
     float4 pa[WPC];
@@ -1208,14 +1378,12 @@ __device__ void gpick_auto(const Grp<GS>& q, const float* buf, const int* ib, in
 }
 
 // The warp's last part: the iterated-bucket fallbacks over re-formed keys where a run overflowed its
-// buffer (fb = 1: every statistic; fb = 2: the spread only), then the depth from FP64 projections of the
-// selected points (as in select_dir).
+// buffer (fb = 1: every statistic; fb = 2: the spread only), then the picks (as in select_dir).
 template <int D>
 __device__ void close_warp(const Grp<32>& q, const KeysW<D>& y, CtlW& C, unsigned* H, float* B0, int* I0, int n,
                            bool ap, int fb, float m1, float m2, int im1, int im2, float p1, float p2, int ip1, int ip2,
-                           int npos, const DsDev& Dd, double yzv, ResDev* __restrict__ out, int* err)
+                           int npos, ResDev* __restrict__ out, int* err)
 {
-    const int g = q.g;
     const int k1 = (n - 1) / 2, k2 = n / 2;
     if (fb) {
         float kl = FLT_MAX, kh = -FLT_MAX;
@@ -1246,30 +1414,13 @@ __device__ void close_warp(const Grp<32>& q, const KeysW<D>& y, CtlW& C, unsigne
                                                                  ip1, ip2, err);
         }
     }
-    const int sel = q.t == 0 ? im1 : (q.t == 1 ? im2 : (q.t == 2 ? ip1 : ip2));
-    if (q.t < 4) C.y64[g][q.t] = sel >= 0 ? proj64(Dd, y.u, sel) : 0.0;
-    q.sync();
-    if (q.t == 0) {
-        const double* Y = C.y64[g];
-        double depth = __longlong_as_double(0x7FF8000000000000LL);
-        if (im1 >= 0 && im2 >= 0) {
-            const double med = (Y[0] + Y[1]) * 0.5;
-            if (ap) {
-                double madp = 0.0;
-                if (npos > 0) madp = ip1 >= 0 && ip2 >= 0 ? fmax(((Y[2] - med) + (Y[3] - med)) * 0.5, 0.0) : depth;
-                depth = depth_from(yzv - med > 0.0 ? yzv - med : 0.0, madp);
-            } else if (ip1 >= 0 && ip2 >= 0) {
-                depth = depth_from(fabs(yzv - med), (fabs(Y[2] - med) + fabs(Y[3] - med)) * 0.5);
-            }
-        }
-        *out = ResDev{depth, -1};
-    }
+    if (q.t == 0) put_picks(out, im1, im2, ap && npos == 0 ? NOPOS : ip1, ap && npos == 0 ? NOPOS : ip2);
 }
 
 template <int D>
 __global__ void __launch_bounds__(WNT, 2) k_pdapw(const TaskDev* __restrict__ tasks, const SlotDev* __restrict__ slots,
                                                    const DsDev* __restrict__ dsets, const float* __restrict__ U,
-                                                   const double* __restrict__ yz, ResDev* __restrict__ res, int* err)
+                                                   ResDev* __restrict__ res, int* err)
 {
     constexpr int DP4 = (D + 3) & ~3;
     constexpr int OFF = 1 << 30;
@@ -1602,7 +1753,7 @@ __global__ void __launch_bounds__(WNT, 2) k_pdapw(const TaskDev* __restrict__ ta
 
     if (w >= GA) return;   // no block barrier follows
     const int64_t ro = S.roff + T.j0 + w;
-    close_warp<D>(q, y, C, H, B0, I0, n, ap, fb, m1, m2, im1, im2, p1, p2, ip1, ip2, npos, Dd, yz[ro], res + ro, err);
+    close_warp<D>(q, y, C, H, B0, I0, n, ap, fb, m1, m2, im1, im2, p1, p2, ip1, ip2, npos, res + ro, err);
 }
 
 }  // namespace
@@ -1788,7 +1939,7 @@ static cudaError_t launch_w(const TaskDev* tasks, int ntasks, const SlotDev* slo
         cudaGetLastError();
         return e;
     }
-    k_pdapw<D><<<ntasks, WNT, smem, st>>>(tasks, slots, ds, U, yz, res, err);
+    k_pdapw<D><<<ntasks, WNT, smem, st>>>(tasks, slots, ds, U, res, err);
     return cudaGetLastError();
 }
 
@@ -1802,7 +1953,7 @@ static cudaError_t launch_t(const TaskDev* tasks, int ntasks, size_t smem, const
         cudaGetLastError();   // do not leave the failure pending for an unrelated later call
         return e;
     }
-    k_pdap2<G, DP4, STREAM><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, yz, res, err, kin);
+    k_pdap2<G, DP4, STREAM><<<ntasks, cta_threads<G>(), smem, st>>>(tasks, slots, ds, U, res, err, kin);
     return cudaGetLastError();
 }
 
@@ -1826,11 +1977,27 @@ int pdap_dp4_class(int d)
     return dp4 <= 16 ? dp4 : 0;
 }
 
+static cudaError_t launch_select(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant,
+                                 const SlotDev* slots, const DsDev* ds, const float* U, const double* yz, ResDev* res,
+                                 int* err, cudaStream_t st, const float* kin);
+
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
                         const DsDev* ds, const float* U, const double* yz, ResDev* res, int* err, cudaStream_t st,
                         const float* kin)
 {
     if (ntasks <= 0) return cudaSuccess;
+    const cudaError_t e = launch_select(tasks, ntasks, smem, group, variant, slots, ds, U, yz, res, err, st, kin);
+    if (e != cudaSuccess) return e;
+    const int64_t threads = (int64_t)ntasks * group * 4;
+    const int nt = 256;
+    k_pdap_finish<<<(unsigned)((threads + nt - 1) / nt), nt, 0, st>>>(tasks, ntasks, group, slots, ds, U, yz, res);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_select(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant,
+                                 const SlotDev* slots, const DsDev* ds, const float* U, const double* yz, ResDev* res,
+                                 int* err, cudaStream_t st, const float* kin)
+{
     if (smem > pdap_smem_limit()) return cudaErrorInvalidValue;
     if (variant & PDAP_WARP) {
         if (group < 1 || group > PDAPW_DIRS) return cudaErrorInvalidValue;

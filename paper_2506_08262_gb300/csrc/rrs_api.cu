@@ -481,7 +481,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c], P.n_pd[c][l], P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
                                      P.d_ds, P.U, P.yz, P.res, ctx->d_err, st));
-                ctx->launches++;
+                ctx->launches += PDAP_LAUNCH_KERNELS;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
                 continue;
             }
@@ -497,7 +497,7 @@ rrs_status enqueue_rounds(rrs_ctx* ctx, Plan& P, cudaStream_t st, bool capturing
                 StageTimer t(ctx, RRS_STAGE_PDAP, st, capturing);
                 CUDA_TRY(launch_pdap(P.d_pd[c] + t0, cnt, P.pd_smem[c], P.pd_group[c], P.pd_variant[c], P.d_slots,
                                      P.d_ds, P.U, P.yz, P.res, ctx->d_err, st, P.keys));
-                ctx->launches += 2;
+                ctx->launches += 1 + PDAP_LAUNCH_KERNELS;
                 ctx->stage_launches[RRS_STAGE_KEYS]++;
                 ctx->stage_launches[RRS_STAGE_PDAP]++;
             }

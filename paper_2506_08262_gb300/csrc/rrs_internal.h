@@ -107,7 +107,10 @@ cudaError_t launch_hd_simt(const TaskDev* tasks, int ntasks, int max_ldx, const 
                            int* err, cudaStream_t st);
 // group: directions per CTA (1, 2 or 4, from pdap_shape); variant: pdap_shape's kernel variant (the key
 // arithmetic class pdap_dp4_class(d), plus PDAP_STREAM), shared by every task
-// yz: the FP64 y_z = u'z of every direction (the direction generator's output), used for the depth
+// yz: the FP64 y_z = u'z of every direction (the direction generator's output), used for the depth.
+// Launches the selection kernel, which writes the points holding the order statistics into the result cells,
+// then k_pdap_finish, which forms the depths from FP64 projections of those points: PDAP_LAUNCH_KERNELS kernels.
+constexpr int PDAP_LAUNCH_KERNELS = 2;
 cudaError_t launch_pdap(const TaskDev* tasks, int ntasks, size_t smem, int group, int variant, const SlotDev* slots,
                         const DsDev* ds, const float* U, const double* yz, ResDev* res, int* err, cudaStream_t st,
                         const float* kin = nullptr);

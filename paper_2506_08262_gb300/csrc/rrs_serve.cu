@@ -509,13 +509,13 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                                        S->st));
                 S_TRY(launch_pdap(tl + t0, cnt, pd_need[key], G, std::get<2>(key), S->d_slots, S->d_ds, S->d_U,
                                   S->d_yz, S->d_res, S->ctx->d_err, S->st, S->d_keys));
-                extra += 2;
+                extra += 1 + PDAP_LAUNCH_KERNELS;
             }
-            extra--;   // counted once below
+            extra -= PDAP_LAUNCH_KERNELS;   // counted once below
         }
         S_TRY(launch_argmin_slotround(S->d_slots, (const int32_t*)(T + o_arg), (int)arg.size(), S->d_U, S->d_res,
                                      S->d_p0, S->d_p1, S->st));
-        S->ctx->launches += 3 + pd.size() + tc.size() + extra;
+        S->ctx->launches += 3 + pd.size() * PDAP_LAUNCH_KERNELS + tc.size() + extra;
         // retire requests whose last round just ran
         std::vector<Request*> still;
         for (size_t ai = 0; ai < na; ++ai) {
