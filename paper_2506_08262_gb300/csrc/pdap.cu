@@ -546,6 +546,26 @@ __device__ __forceinline__ float key_halves(const float* u, const float* x)
     return __fadd_rn(p0, p1);
 }
 
+// Row i of X as D4 floats (D4 <= ldx, the padding zero): from the dataset's tiled copy Xt when it keeps
+// one, else from the padded rows; the same values either way.  The projection pass streams X once per CTA
+// and is bound by the cache lines its loads touch: a warp reading chunk c of 32 consecutive rows reads 512
+// contiguous bytes of Xt, where in the padded rows the same 32 chunks lie on every line of the 32 rows.
+template <int D4>
+__device__ __forceinline__ void load_row(const DsDev& D, int i, int ldx, float (&xv)[D4])
+{
+    const float4* xr = D.Xt ? reinterpret_cast<const float4*>(D.Xt) + ((int64_t)(i >> 5) * (ldx >> 2)) * 32 + (i & 31)
+                            : reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
+    const int cs = D.Xt ? 32 : 1;   // float4 stride between the chunks of one row
+#pragma unroll
+    for (int c = 0; c < D4 / 4; ++c) {
+        const float4 t4 = xr[c * cs];
+        xv[4 * c] = t4.x;
+        xv[4 * c + 1] = t4.y;
+        xv[4 * c + 2] = t4.z;
+        xv[4 * c + 3] = t4.w;
+    }
+}
+
 // One direction's keys held in an array: shared memory (resident keys) or device memory (keys formed
 // by launch_pdap_keys when they do not fit shared memory).
 struct KeysArray {
@@ -731,7 +751,7 @@ __global__ void __launch_bounds__(256) k_pdap_finish(const TaskDev* __restrict__
     ResDev* cell = nullptr;
     if (live) {
         const SlotDev& S = slots[T.slot];
-        const DsDev& D = dsets[S.ds];
+        const DsDev& D = dsets[T.ds];
         cell = res + S.roff + T.j0 + g;
         a = reinterpret_cast<const int2*>(cell)[0];
         b = reinterpret_cast<const int2*>(cell)[1];
@@ -1002,7 +1022,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     __shared__ Ctl C;
     const TaskDev T = tasks[blockIdx.x];
     const SlotDev& S = slots[T.slot];
-    const DsDev D = dsets[S.ds];
+    const DsDev D = dsets[T.ds];   // the task carries its dataset row, so both loads go out together
     const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = DP4 ? DP4 : ((d + 3) & ~3);
     const bool ap = (S.kind == 2);
     const int tid = threadIdx.x;
@@ -1027,7 +1047,23 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     if ((tid >> 5) < G) {
         const int g = tid >> 5, lane = tid & 31;
         float yc = 0.0f, qf = 0.0f;
-        if (g < GA) {   // inert directions keep a zero direction, as staged
+        if (g < GA && d <= 32) {
+            // lane r holds u_r and forms (Cov u)_r from the other lanes' u_c: every load of the warp is
+            // independent of the arithmetic, so they go out together
+            const float* u = U + S.uoff + (int64_t)(T.j0 + g) * ldx;
+            const float ur = lane < d ? u[lane] : 0.0f;
+            if (lane < d) yc = __fmul_rn(ur, D.center[lane]);
+            if (D.cov) {
+                const float* crow = D.cov + lane * d;
+                float w = 0.0f;
+#pragma unroll 8
+                for (int c = 0; c < d; ++c) {
+                    const float uc = __shfl_sync(0xFFFFFFFFu, ur, c);
+                    if (lane < d) w = fmaf(crow[c], uc, w);
+                }
+                qf = __fmul_rn(w, ur);
+            }
+        } else if (g < GA) {   // inert directions keep a zero direction, as staged
             const float* u = U + S.uoff + (int64_t)(T.j0 + g) * ldx;
             for (int r = lane; r < d; r += 32) yc = fmaf(u[r], D.center[r], yc);
             if (D.cov) {
@@ -1104,16 +1140,8 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
             }
             const float sca = sc[2 * pair], ofa = of[2 * pair], scb = sc[2 * pair + 1], ofb = of[2 * pair + 1];
             for (int i = tid >> 1; i < n; i += NTK / 2) {
-                const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
                 float xv[D4];
-#pragma unroll
-                for (int c = 0; c < D4 / 4; ++c) {
-                    const float4 t4 = xr[c];
-                    xv[4 * c] = t4.x;
-                    xv[4 * c + 1] = t4.y;
-                    xv[4 * c + 2] = t4.z;
-                    xv[4 * c + 3] = t4.w;
-                }
+                load_row<D4>(D, i, ldx, xv);
                 const float ka = key_halves<D4>(ua, xv), kb = key_halves<D4>(ub, xv);
                 if (!STREAM) keys[(size_t)(2 * pair) * npad + i] = ka;
                 atomicAdd(&hist[(2 * pair) * NB + bucket_m(ka, sca, ofa)], 1u);
@@ -1127,36 +1155,24 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
 #pragma unroll
                 for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
             // two points per iteration: both rows' loads are in flight together
+            constexpr int D4 = DP4 > 0 ? DP4 : 4;
             for (int i = tid; i < n; i += 2 * NTK) {
                 const int i2 = i + NTK;
                 const bool two = i2 < n;
-                const float4* xa = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
-                const float4* xb = reinterpret_cast<const float4*>(D.X32 + (int64_t)(two ? i2 : i) * ldx);
-                float4 va[DP4 > 0 ? DP4 / 4 : 1], vb[DP4 > 0 ? DP4 / 4 : 1];
-#pragma unroll
-                for (int c = 0; c < DP4 / 4; ++c) {
-                    va[c] = xa[c];
-                    vb[c] = xb[c];
-                }
+                float xa_[D4], xb_[D4];
+                load_row<D4>(D, i, ldx, xa_);
+                load_row<D4>(D, two ? i2 : i, ldx, xb_);
                 float acc[G], acc2[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     // key_halves on the register copies (one row's dims as plain floats)
-                    float uu[DP4 > 0 ? DP4 : 4], xa_[DP4 > 0 ? DP4 : 4], xb_[DP4 > 0 ? DP4 : 4];
+                    float uu[D4];
 #pragma unroll
                     for (int c = 0; c < DP4 / 4; ++c) {
                         uu[4 * c] = ur[g][c].x;
                         uu[4 * c + 1] = ur[g][c].y;
                         uu[4 * c + 2] = ur[g][c].z;
                         uu[4 * c + 3] = ur[g][c].w;
-                        xa_[4 * c] = va[c].x;
-                        xa_[4 * c + 1] = va[c].y;
-                        xa_[4 * c + 2] = va[c].z;
-                        xa_[4 * c + 3] = va[c].w;
-                        xb_[4 * c] = vb[c].x;
-                        xb_[4 * c + 1] = vb[c].y;
-                        xb_[4 * c + 2] = vb[c].z;
-                        xb_[4 * c + 3] = vb[c].w;
                     }
                     acc[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xa_);
                     acc2[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xb_);

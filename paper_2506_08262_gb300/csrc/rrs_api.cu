@@ -222,6 +222,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
             const Dataset& D = *R.dset;
             DsDev dd{};
             dd.X32 = D.X32;
+            dd.Xt = D.Xt;
             dd.X64 = D.X64;
             dd.xnorm = D.xnorm;
             dd.Xbf = D.Xbf;
@@ -329,7 +330,7 @@ rrs_status build_plan(const std::vector<ReqView>& reqs, Plan& P)
                     for (int j0 = 0; j0 < m; j0 += per) P.hd_tasks.push_back(TaskDev{s, j0, std::min(per, m - j0), 0});
                 }
             } else {
-                for (int j0 = 0; j0 < m; j0 += G) P.pd_tasks[cls].push_back(TaskDev{s, j0, std::min(G, m - j0), 0});
+                for (int j0 = 0; j0 < m; j0 += G) P.pd_tasks[cls].push_back(TaskDev{s, j0, std::min(G, m - j0), S.ds});
             }
             P.argmin_list.push_back(s);
         }
@@ -575,6 +576,7 @@ rrs_status rrs_destroy(rrs_ctx* ctx)
     cudaDeviceSynchronize();
     for (auto& kv : ctx->datasets) {
         cudaFree(kv.second.X32);
+        cudaFree(kv.second.Xt);
         cudaFree(kv.second.X64);
         cudaFree(kv.second.xnorm);
         cudaFree(kv.second.Xbf);
@@ -611,7 +613,10 @@ rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t 
                  bn = sizeof(float) * n;
     const bool want_cov = d <= RRS_COV_MAX_D;
     const size_t bmom = sizeof(float) * ((size_t)d + (want_cov ? (size_t)d * d : 0) + 1);
-    D.bytes = b32 + b64 + bn + bmom;
+    // the rows again in 32-row tiles for the selection kernels' projection pass (d <= 16: the kernels that
+    // hold directions in registers), which streams X once per CTA and is bound by the cache lines its loads touch
+    const size_t bt = d <= 16 ? sizeof(float) * tile_rows_floats(n, D.ldx) : 0;
+    D.bytes = b32 + bt + b64 + bn + bmom;
     if (!budget_ok(ctx, D.bytes)) return fail(RRS_ERR_BUDGET, "dataset needs %zu bytes", D.bytes);
     void* staged = nullptr;
     const void* src = X;
@@ -622,11 +627,16 @@ rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t 
         src = staged;
     }
     cudaError_t e = cudaMalloc(&D.X32, b32);
+    if (e == cudaSuccess && bt) e = cudaMalloc(&D.Xt, bt);
     if (e == cudaSuccess && b64) e = cudaMalloc(&D.X64, b64);
     if (e == cudaSuccess) e = cudaMalloc(&D.xnorm, bn);
     if (e == cudaSuccess) e = cudaMalloc(&D.center, bmom);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = launch_convert_dataset(src, dtype, n, d, D.ldx, D.X32, D.X64, D.xnorm, ctx->d_err, st);
+    if (e == cudaSuccess && D.Xt) {
+        e = launch_tile_rows(D.X32, n, D.ldx, D.Xt, st);
+        ctx->launches++;
+    }
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&bad, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -642,6 +652,7 @@ rrs_status rrs_register_dataset(rrs_ctx* ctx, const void* X, int64_t n, int32_t 
     if (e != cudaSuccess || bad) {
         cudaGetLastError();
         cudaFree(D.X32);
+        cudaFree(D.Xt);
         cudaFree(D.X64);
         cudaFree(D.xnorm);
         cudaFree(D.center);
@@ -664,6 +675,7 @@ rrs_status rrs_free(rrs_ctx* ctx, int64_t dataset_id)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     cudaFree(it->second.X32);
+    cudaFree(it->second.Xt);
     cudaFree(it->second.X64);
     cudaFree(it->second.xnorm);
     cudaFree(it->second.Xbf);

@@ -20,6 +20,7 @@ struct Dataset {
     int32_t ldx = 0;
     int32_t kp = 0;
     float* X32 = nullptr;
+    float* Xt = nullptr;       // d <= 16: the FP32 rows in 32-row tiles, 16-byte chunks interleaved (tile_rows)
     double* X64 = nullptr;
     float* xnorm = nullptr;
     uint16_t* Xbf = nullptr;

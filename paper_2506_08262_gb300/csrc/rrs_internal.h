@@ -13,6 +13,11 @@ namespace rrs {
 // A resident dataset, as the kernels see it.
 struct DsDev {
     const float* X32;      // n x ldx FP32 rows, zero padded
+    // Xt: the FP32 rows again, for the selection kernels' projection pass (d <= 16), or nullptr.  Rows come in
+    // tiles of 32 (the last one zero padded); within a tile, 16-byte chunk c of its 32 rows is contiguous:
+    // float4 index ((i / 32) * (ldx / 4) + c) * 32 + i % 32.  A warp reading chunk c of 32 consecutive rows
+    // then reads 512 contiguous bytes (4 cache lines) where padded rows spread it over all 12 lines of d = 10.
+    const float* Xt;
     const double* X64;     // n x d FP64 rows, or nullptr if the data came in FP32
     const float* xnorm;    // n Euclidean row norms, rounded up
     const uint16_t* Xbf;   // n x (2*kp) BF16 planes [x_hi | x_lo] for the tensor-core path, or nullptr
@@ -62,7 +67,7 @@ struct TaskDev {
     int32_t slot;
     int32_t j0;
     int32_t nj;
-    int32_t pad;
+    int32_t ds;            // selection tasks: the slot's dataset row (read beside the slot, not after it); else 0
 };
 
 // Per (slot, direction) result of one round.
@@ -140,6 +145,9 @@ cudaError_t launch_debug_dirs(uint64_t seed, int q, int round0, int m, int d, fl
                               float* U, cudaStream_t st);
 cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, int ldx, float* X32,
                                    double* X64, float* xnorm, int* bad, cudaStream_t st);
+// DsDev::Xt from the padded rows X32 (Xt holds tile_rows_floats(n, ldx) floats)
+size_t tile_rows_floats(int64_t n, int ldx);
+cudaError_t launch_tile_rows(const float* X32, int64_t n, int ldx, float* Xt, cudaStream_t st);
 // mean, covariance (d <= RRS_COV_MAX_D) and radius about the mean of the FP32 rows; rc_out is a device float
 cudaError_t launch_moments(const float* X32, int64_t n, int d, int ldx, float* center, float* cov, float* rc_out,
                            cudaStream_t st);

@@ -55,6 +55,30 @@ cudaError_t launch_convert_dataset(const void* X, int dtype, int64_t n, int d, i
     return cudaGetLastError();
 }
 
+// One thread per (row, 16-byte chunk) of the tiled copy, rows beyond n zero.
+__global__ void k_tile_rows(const float4* __restrict__ X32, int64_t n, int c4, int64_t total, float4* __restrict__ Xt)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t lane = e & 31, rest = e >> 5;
+    const int64_t c = rest % c4, tile = rest / c4;
+    const int64_t i = tile * 32 + lane;
+    Xt[e] = i < n ? X32[i * c4 + c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+size_t tile_rows_floats(int64_t n, int ldx)
+{
+    return (size_t)((n + 31) / 32) * 32 * (size_t)ldx;
+}
+
+cudaError_t launch_tile_rows(const float* X32, int64_t n, int ldx, float* Xt, cudaStream_t st)
+{
+    const int64_t total = (int64_t)(tile_rows_floats(n, ldx) / 4);
+    const int nt = 256;
+    k_tile_rows<<<(unsigned)((total + nt - 1) / nt), nt, 0, st>>>((const float4*)X32, n, ldx / 4, total, (float4*)Xt);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // data moments (range heuristics of the selection kernel only; no result
 // depends on their accuracy)

@@ -162,6 +162,7 @@ rrs_status ensure_dataset(rrs_server* S, int64_t id, int* row)
     }
     DsDev dd{};
     dd.X32 = D.X32;
+    dd.Xt = D.Xt;
     dd.X64 = D.X64;
     dd.xnorm = D.xnorm;
     dd.Xbf = D.Xbf;
@@ -446,7 +447,7 @@ rrs_status rrs_server_step(rrs_server* S, int32_t* active_queries_out, int32_t* 
                     auto& v = pd[key];
                     size_t& need = pd_need[key];
                     need = std::max(need, sh.smem);
-                    for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), 0});
+                    for (int j0 = 0; j0 < R->m; j0 += G) v.push_back(TaskDev{slot, j0, std::min(G, R->m - j0), row});
                 }
                 arg.push_back(slot);
             }
