@@ -631,21 +631,20 @@ __device__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, i
 {
     if (q.t == 0) C.f_b1[q.g] = NB;
     q.sync();
-    // the window count is non-decreasing in s: each thread tests its PER values of s with independent
-    // loads and offers the first that exceeds k2
-    constexpr int PER = NB / GS;
-    int first = NB;
-#pragma unroll
-    for (int k = PER - 1; k >= 0; --k) {
-        const int s = q.t * PER + k;
+    // the window count is non-decreasing in s: rounds of GS consecutive values of s, one per thread, so
+    // consecutive threads read consecutive prefix counts (no bank conflicts), until one exceeds k2; it
+    // does by s = NB - 1, where the window holds all n keys
+    int ss = NB;
+    for (int s0 = 0; s0 < NB; s0 += GS) {
+        const int s = s0 + q.t;
         const int hi = bb + s < NB - 1 ? bb + s : NB - 1, lo = ba - s;
         const int c = (int)H[hi] - (lo >= 1 ? (int)H[lo - 1] : 0);
-        if (c > k2) first = s;
+        if (c > k2) atomicMin(&C.f_b1[q.g], s);
+        q.sync();
+        ss = C.f_b1[q.g];
+        q.sync();
+        if (ss < NB) break;
     }
-    if (first < NB) atomicMin(&C.f_b1[q.g], first);
-    q.sync();
-    const int ss = C.f_b1[q.g];
-    q.sync();
     const int w = bb - ba + 1;
     const int L0 = ba - ss - w - 2, L1 = ba - ss + w + 3, R0 = bb + ss - w - 3, R1 = bb + ss + w + 2;
     if (ss >= w + 4 && L0 >= 1 && R1 <= NB - 2) {
