@@ -56,10 +56,10 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # valid only for the kernel source it was taken from: `src_sha16` is the SHA-256 prefix of those files at
 # capture time, and a mismatch (the kernel changed since) reports null.
 CAPTURED = {
-    # k_pdap2<2,12>, d = 10, n = 10,000, 50,000 directions per launch: the 40 launches of one step (both kinds,
-    # 20 rounds each): DRAM bytes and warp instructions per (point, direction) element, averaged
+    # k_pdap2<2,12>, d = 10, n = 10,000, 50,000 directions per launch: rounds 10-12 of each kind (six launches
+    # of the first warm-up step): DRAM bytes and warp instructions per (point, direction) element, averaged
     "k_pdap2_c2": {"src": ("paper_2506_08262_gb300/csrc/pdap.cu", "paper_2506_08262_gb300/csrc/rrs_internal.h"),
-                   "src_sha16": "c190a3de1b59fa1c", "traffic": 3.967e6, "warp_instr_per_element": 2.287},
+                   "src_sha16": "b1095d24331c8f9a", "traffic": 3.534e6, "warp_instr_per_element": 2.535},
     # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50: one launch
     "k_hd_tc_c3": {"src": ("paper_2506_08262_gb300/csrc/hd_tc.cu", "paper_2506_08262_gb300/csrc/async_sync.cuh",
                            "paper_2506_08262_gb300/csrc/rrs_device.cuh"),
