@@ -566,6 +566,64 @@ __device__ __forceinline__ void load_row(const DsDev& D, int i, int ldx, float (
     }
 }
 
+// Pass A of k_pdap2 for d <= 16 (D4 = d rounded up to 4, the directions uu in registers): the keys of G
+// directions for the points i = tid + k NTK, stored (unless STREAM) and counted in the directions' histograms.
+// xp points at row tid; CS is the float4 distance between the 16-byte chunks of one row (32 in the tiled
+// copy Xt, 1 in the padded rows).  In both layouts rows i and i + NTK lie rstep = NTK ldx / 4 float4 apart
+// (NTK is a multiple of 32, so i mod 32 stays put within a tile), so a thread walks its rows by a pointer
+// increment and every chunk load takes a constant offset.  Two rows per iteration keep six loads in flight.
+template <int G, int D4, bool STREAM, int CS, int NTK>
+__device__ __forceinline__ void pass_a_rows(const float4* __restrict__ xp, size_t rstep, int tid, int n, int npad,
+                                            const float (&uu)[G][D4], const float (&sc)[G], const float (&of)[G],
+                                            float* keys, unsigned* hist)
+{
+    float* kq = keys + tid;   // key of direction g for the thread's current row: kq[g * npad]
+    int i = tid;
+    for (; i + NTK < n; i += 2 * NTK, xp += 2 * rstep, kq += 2 * NTK) {
+        const float4* xq = xp + rstep;
+        float xa[D4], xb[D4];
+#pragma unroll
+        for (int c = 0; c < D4 / 4; ++c) {
+            const float4 a = xp[c * CS], b = xq[c * CS];
+            xa[4 * c] = a.x;
+            xa[4 * c + 1] = a.y;
+            xa[4 * c + 2] = a.z;
+            xa[4 * c + 3] = a.w;
+            xb[4 * c] = b.x;
+            xb[4 * c + 1] = b.y;
+            xb[4 * c + 2] = b.z;
+            xb[4 * c + 3] = b.w;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ka = key_halves<D4>(uu[g], xa), kb = key_halves<D4>(uu[g], xb);
+            if (!STREAM) {
+                kq[g * npad] = ka;
+                kq[g * npad + NTK] = kb;
+            }
+            atomicAdd(&hist[g * NB + bucket_m(ka, sc[g], of[g])], 1u);
+            atomicAdd(&hist[g * NB + bucket_m(kb, sc[g], of[g])], 1u);
+        }
+    }
+    if (i < n) {
+        float xa[D4];
+#pragma unroll
+        for (int c = 0; c < D4 / 4; ++c) {
+            const float4 a = xp[c * CS];
+            xa[4 * c] = a.x;
+            xa[4 * c + 1] = a.y;
+            xa[4 * c + 2] = a.z;
+            xa[4 * c + 3] = a.w;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float ka = key_halves<D4>(uu[g], xa);
+            if (!STREAM) kq[g * npad] = ka;
+            atomicAdd(&hist[g * NB + bucket_m(ka, sc[g], of[g])], 1u);
+        }
+    }
+}
+
 // One direction's keys held in an array: shared memory (resident keys) or device memory (keys formed
 // by launch_pdap_keys when they do not fit shared memory).
 struct KeysArray {
@@ -787,6 +845,58 @@ __global__ void __launch_bounds__(256) k_pdap_finish(const TaskDev* __restrict__
 //   D_P     a |y - med| histogram pass, then the gather and ranking of the MAD run;
 //   D_AP    in the median's gather pass, the run of the MAD_+ ranks guessed for no key tying the median.
 // Runs that overflow the gather buffer fall back to iterated bucket selection.
+// The gather pass of select_dir: every key whose raw bucket value lies in the median run [ml, ml + wm]
+// moves, with its point index, to (B0, I0); every key in one of the NR2 second runs [l1, l1 + w1],
+// [l2, l2 + w2] to (B1, I1) (ranges of raw values, compared as unsigned differences).  Four keys are
+// tested at once with no branch; only a group of four holding a gathered key takes the slow path, which
+// repeats the tests key by key.  The keys gathered, and so the picks, are those of a test key by key.
+template <int GS, int NR2, class K>
+__device__ __forceinline__ void gather_runs(const Grp<GS>& q, const K& y, int n, float sc, float of, int ml,
+                                            unsigned wm, int l1, unsigned w1, int l2, unsigned w2, int* fill,
+                                            float* B0, int* I0, float* B1, int* I1)
+{
+    auto in0 = [&](int rv) { return (unsigned)rv - (unsigned)ml <= wm; };
+    auto in1 = [&](int rv) {
+        bool h = false;
+        if (NR2 >= 1) h = (unsigned)rv - (unsigned)l1 <= w1;
+        if (NR2 >= 2) h = h | ((unsigned)rv - (unsigned)l2 <= w2);
+        return h;
+    };
+    auto put = [&](float v, int rv, int i) {
+        if (in0(rv)) {
+            const int pos = atomicAdd(&fill[0], 1);
+            if (pos < CAP) {
+                B0[pos] = v;
+                I0[pos] = i;
+            }
+        }
+        if (NR2 > 0 && in1(rv)) {
+            const int pos = atomicAdd(&fill[1], 1);
+            if (pos < CAP1) {
+                B1[pos] = v;
+                I1[pos] = i;
+            }
+        }
+    };
+    const int n4 = n & ~3;
+    for (int i = 4 * q.t; i < n4; i += 4 * GS) {
+        const float4 y4 = y.get4(i);
+        const int r0 = bucket_raw(y4.x, sc, of), r1 = bucket_raw(y4.y, sc, of), r2 = bucket_raw(y4.z, sc, of),
+                  r3 = bucket_raw(y4.w, sc, of);
+        const bool hit = (in0(r0) | in0(r1) | in0(r2) | in0(r3)) | (in1(r0) | in1(r1) | in1(r2) | in1(r3));
+        if (hit) {
+            put(y4.x, r0, i);
+            put(y4.y, r1, i + 1);
+            put(y4.z, r2, i + 2);
+            put(y4.w, r3, i + 3);
+        }
+    }
+    for (int i = n4 + q.t; i < n; i += GS) {
+        const float v = y.get(i);
+        put(v, bucket_raw(v, sc, of), i);
+    }
+}
+
 template <int GS, class K>
 __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C, unsigned* H, float* B0, int* I0,
                                            int n, bool ap, const DsDev& D, int64_t roff, ResDev* __restrict__ res,
@@ -840,36 +950,20 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
     if (!fb) {
         if (q.t < 2) C.fill[g][q.t] = 0;
         q.sync();
-        // the runs as ranges of raw bucket values (signed compares; the edge buckets take every value
-        // clamped into them)
-        const int ml = raw_lo(ba), mh = raw_hi(bb);
-        const int xl1 = second ? raw_lo(r2.x) : INT_MAX, xh1 = second ? raw_hi(r2.y) : INT_MIN;
-        const int xl2 = r2.z <= r2.w ? raw_lo(r2.z) : INT_MAX, xh2 = r2.z <= r2.w ? raw_hi(r2.w) : INT_MIN;
-        auto gather = [&](float v, int i) {
-            const int rv = bucket_raw(v, sc, of);
-            if (rv >= ml && rv <= mh) {
-                const int pos = atomicAdd(&C.fill[g][0], 1);
-                if (pos < CAP) {
-                    B0[pos] = v;
-                    I0[pos] = i;
-                }
-            }
-            if ((rv >= xl1 && rv <= xh1) || (rv >= xl2 && rv <= xh2)) {
-                const int pos = atomicAdd(&C.fill[g][1], 1);
-                if (pos < CAP1) {
-                    B1[pos] = v;
-                    I1[pos] = i;
-                }
-            }
-        };
-        for (int i = 4 * q.t; i < n4; i += 4 * GS) {
-            const float4 y4 = y.get4(i);
-            gather(y4.x, i);
-            gather(y4.y, i + 1);
-            gather(y4.z, i + 2);
-            gather(y4.w, i + 3);
-        }
-        for (int i = n4 + q.t; i < n; i += GS) gather(y.get(i), i);
+        // the runs as ranges of raw bucket values (the edge buckets take every value clamped into them)
+        const int ml = raw_lo(ba);
+        const unsigned wm = (unsigned)raw_hi(bb) - (unsigned)ml;
+        const bool two_runs = second && r2.z <= r2.w;
+        const int l1 = second ? raw_lo(r2.x) : 0, l2 = two_runs ? raw_lo(r2.z) : 0;
+        const unsigned w1 = second ? (unsigned)raw_hi(r2.y) - (unsigned)l1 : 0u;
+        const unsigned w2 = two_runs ? (unsigned)raw_hi(r2.w) - (unsigned)l2 : 0u;
+        int* fill = &C.fill[g][0];
+        if (two_runs)
+            gather_runs<GS, 2>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
+        else if (second)
+            gather_runs<GS, 1>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
+        else
+            gather_runs<GS, 0>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
         q.sync();
         gpick(q, B0, I0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2, im1, im2);
         if (ap) {
@@ -1148,37 +1242,27 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 atomicAdd(&hist[(2 * pair + 1) * NB + bucket_m(kb, scb, ofb)], 1u);
             }
         } else if (DP4 > 0) {
-            float4 ur[G][DP4 > 0 ? DP4 / 4 : 1];
+            constexpr int D4 = DP4 > 0 ? DP4 : 4;
+            float uu[G][D4];
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
-                for (int c = 0; c < DP4 / 4; ++c) ur[g][c] = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
-            // two points per iteration: both rows' loads are in flight together
-            constexpr int D4 = DP4 > 0 ? DP4 : 4;
-            for (int i = tid; i < n; i += 2 * NTK) {
-                const int i2 = i + NTK;
-                const bool two = i2 < n;
-                float xa_[D4], xb_[D4];
-                load_row<D4>(D, i, ldx, xa_);
-                load_row<D4>(D, two ? i2 : i, ldx, xb_);
-                float acc[G], acc2[G];
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    // key_halves on the register copies (one row's dims as plain floats)
-                    float uu[D4];
-#pragma unroll
-                    for (int c = 0; c < DP4 / 4; ++c) {
-                        uu[4 * c] = ur[g][c].x;
-                        uu[4 * c + 1] = ur[g][c].y;
-                        uu[4 * c + 2] = ur[g][c].z;
-                        uu[4 * c + 3] = ur[g][c].w;
-                    }
-                    acc[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xa_);
-                    acc2[g] = key_halves<(DP4 > 0 ? DP4 : 4)>(uu, xb_);
+                for (int c = 0; c < D4 / 4; ++c) {
+                    const float4 u4 = *reinterpret_cast<const float4*>(uS + g * ldx + 4 * c);
+                    uu[g][4 * c] = u4.x;
+                    uu[g][4 * c + 1] = u4.y;
+                    uu[g][4 * c + 2] = u4.z;
+                    uu[g][4 * c + 3] = u4.w;
                 }
-                emit(i, acc);
-                if (two) emit(i2, acc2);
-            }
+            const int c4 = ldx >> 2;
+            const size_t rstep = (size_t)NTK * c4;
+            if (D.Xt)
+                pass_a_rows<G, D4, STREAM, 32, NTK>(reinterpret_cast<const float4*>(D.Xt) +
+                                                        ((size_t)(tid >> 5) * c4 * 32 + (tid & 31)),
+                                                    rstep, tid, n, npad, uu, sc, of, keys, hist);
+            else
+                pass_a_rows<G, D4, STREAM, 1, NTK>(reinterpret_cast<const float4*>(D.X32) + (size_t)tid * c4, rstep,
+                                                   tid, n, npad, uu, sc, of, keys, hist);
         } else {
             for (int i = tid; i < n; i += NTK) {
                 const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
