@@ -44,7 +44,10 @@ __host__ __device__ constexpr int cta_threads()
 constexpr int NB = 2048;     // buckets per direction
 constexpr int CAP = 256;     // gathered keys per direction: the median run (and the D_AP MAD_+ run)
 constexpr int CAP1 = 512;    // second gather buffer: the D_AP MAD_+ run or the D_P MAD runs L, R
+constexpr int CAP1H = (NB - 256) / 2;   // D_P runs too large for it: pairs in the histogram area (after 256 counters)
 constexpr int MAXG = 4;
+// Stride of the resident keys of one direction in shared memory: n rounded up to 32 floats (128 bytes)
+__host__ __device__ constexpr int pdap_key_stride(int n) { return (n + 31) & ~31; }
 constexpr int FB_NB = NB;    // fallback histogram (reuses the bucket area)
 constexpr int FB_CAP = CAP + CAP1;  // fallback gather buffer: a direction's two gather areas
 
@@ -135,7 +138,7 @@ __device__ __forceinline__ float warp_min(float v)
 
 // Group sum of one int per thread (every thread gets the total).
 template <int GS, class CT>
-__device__ int gsum(const Grp<GS>& q, int c, CT& C)
+__device__ __forceinline__ int gsum(const Grp<GS>& q, int c, CT& C)
 {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
@@ -171,7 +174,7 @@ __device__ void gminmax(const Grp<GS>& q, float lo, float hi, CT& C, float& olo,
 
 // Group min and max of two pairs at once (one barrier round for both).
 template <int GS, class CT>
-__device__ void gminmax2(const Grp<GS>& q, float& lo1, float& hi1, float& lo2, float& hi2, CT& C)
+__device__ __forceinline__ void gminmax2(const Grp<GS>& q, float& lo1, float& hi1, float& lo2, float& hi2, CT& C)
 {
     constexpr int NW = GS / 32;   // at most 16: 4 NW values fit the 2 NWARP cells of fred
     static_assert(4 * NW <= 2 * NWARP, "gminmax2 scratch");
@@ -260,7 +263,7 @@ __device__ void gfind(const Grp<GS>& q, const unsigned* h, int ra, int rb, CT& C
 // each, the bucket, the keys below it and the keys in it.  With PREFIX, h becomes its inclusive prefix
 // counts in the same pass.
 template <int GS, int NR, bool PREFIX>
-__device__ void gfindn(const Grp<GS>& q, unsigned* h, const int (&rk)[NR], Ctl& C, int (&bo)[NR], int (&co)[NR],
+__device__ __forceinline__ void gfindn(const Grp<GS>& q, unsigned* h, const int (&rk)[NR], Ctl& C, int (&bo)[NR], int (&co)[NR],
                        int (&ho)[NR])
 {
     constexpr int PER = NB / GS;
@@ -371,6 +374,7 @@ __device__ void gpick(const Grp<GS>& q, const float* buf, const int* ib, int cnt
 // them there.  Buckets are monotone in the value, so the rank of a pair is the count in lower buckets
 // plus its rank within its own bucket.
 constexpr int NB2 = 256;
+static_assert(NB2 + 2 * CAP1H == NB, "D_P runs in the histogram area: NB2 counters, then CAP1H values and CAP1H indices");
 template <int GS, class CT, int TCAP = CAP>
 __device__ void gpick_wide(const Grp<GS>& q, const float* buf, const int* ib, int cnt, int s1, int s2, float lo,
                            float hi, unsigned* h2, float* tb, int* ti, CT& C, float& o1, float& o2, int& i1,
@@ -427,6 +431,10 @@ __device__ void gpick_wide(const Grp<GS>& q, const float* buf, const int* ib, in
     q.sync();
     const int b1 = C.f_b1[q.g], c1 = C.f_c1[q.g], b2 = C.f_b2[q.g];
     const int n2 = C.f_c2[q.g] + (int)h2[b2] - c1;
+    if (n2 > TCAP) {   // the rank buckets hold more pairs than (tb, ti): rank the whole set
+        gpick(q, buf, ib, cnt, s1, s2, C, o1, o2, i1, i2);
+        return;
+    }
     for (int t = q.t; t < cnt; t += GS) {
         const float v = buf[t];
         const int b = bk(v);
@@ -573,11 +581,11 @@ __device__ __forceinline__ void load_row(const DsDev& D, int i, int ldx, float (
 // (NTK is a multiple of 32, so i mod 32 stays put within a tile), so a thread walks its rows by a pointer
 // increment and every chunk load takes a constant offset.  Two rows per iteration keep six loads in flight.
 template <int G, int D4, bool STREAM, int CS, int NTK>
-__device__ __forceinline__ void pass_a_rows(const float4* __restrict__ xp, size_t rstep, int tid, int n, int npad,
+__device__ __forceinline__ void pass_a_rows(const float4* __restrict__ xp, size_t rstep, int tid, int n, int kst,
                                             const float (&uu)[G][D4], const float (&sc)[G], const float (&of)[G],
                                             float* keys, unsigned* hist)
 {
-    float* kq = keys + tid;   // key of direction g for the thread's current row: kq[g * npad]
+    float* kq = keys + tid;   // key of direction g for the thread's current row: kq[g * kst]
     int i = tid;
     for (; i + NTK < n; i += 2 * NTK, xp += 2 * rstep, kq += 2 * NTK) {
         const float4* xq = xp + rstep;
@@ -598,8 +606,8 @@ __device__ __forceinline__ void pass_a_rows(const float4* __restrict__ xp, size_
         for (int g = 0; g < G; ++g) {
             const float ka = key_halves<D4>(uu[g], xa), kb = key_halves<D4>(uu[g], xb);
             if (!STREAM) {
-                kq[g * npad] = ka;
-                kq[g * npad + NTK] = kb;
+                kq[g * kst] = ka;
+                kq[g * kst + NTK] = kb;
             }
             atomicAdd(&hist[g * NB + bucket_m(ka, sc[g], of[g])], 1u);
             atomicAdd(&hist[g * NB + bucket_m(kb, sc[g], of[g])], 1u);
@@ -618,7 +626,7 @@ __device__ __forceinline__ void pass_a_rows(const float4* __restrict__ xp, size_
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const float ka = key_halves<D4>(uu[g], xa);
-            if (!STREAM) kq[g * npad] = ka;
+            if (!STREAM) kq[g * kst] = ka;
             atomicAdd(&hist[g * NB + bucket_m(ka, sc[g], of[g])], 1u);
         }
     }
@@ -684,7 +692,7 @@ struct KeysRecomputed {
 // R = [R0, R1] above it.  H holds inclusive prefix counts (gfindn with PREFIX).  The runs stay unset (r untouched) when they would
 // overlap the median run or the edge buckets, or hold more than cap keys.
 template <int GS, class CT>
-__device__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, int k2, int cap, int4& r,
+__device__ __forceinline__ void mad_runs(const Grp<GS>& q, unsigned* H, CT& C, int ba, int bb, int k2, int cap, int4& r,
                          int& cnt1, int& c_in)
 {
     if (q.t == 0) C.f_b1[q.g] = NB;
@@ -847,13 +855,15 @@ __global__ void __launch_bounds__(256) k_pdap_finish(const TaskDev* __restrict__
 // Runs that overflow the gather buffer fall back to iterated bucket selection.
 // The gather pass of select_dir: every key whose raw bucket value lies in the median run [ml, ml + wm]
 // moves, with its point index, to (B0, I0); every key in one of the NR2 second runs [l1, l1 + w1],
-// [l2, l2 + w2] to (B1, I1) (ranges of raw values, compared as unsigned differences).  Four keys are
-// tested at once with no branch; only a group of four holding a gathered key takes the slow path, which
-// repeats the tests key by key.  The keys gathered, and so the picks, are those of a test key by key.
+// [l2, l2 + w2] to (B1, I1), which holds cap1 pairs (ranges of raw values, compared as unsigned
+// differences).  Four keys are tested at once with no branch into a mask of eight bits (key k in the median
+// run, in a second run); a thread then takes one pass per set bit, so a warp spends on the rare gathered keys
+// only as many passes as its busiest thread.  The keys gathered, and so the picks, are those of a test key by
+// key.
 template <int GS, int NR2, class K>
 __device__ __forceinline__ void gather_runs(const Grp<GS>& q, const K& y, int n, float sc, float of, int ml,
                                             unsigned wm, int l1, unsigned w1, int l2, unsigned w2, int* fill,
-                                            float* B0, int* I0, float* B1, int* I1)
+                                            float* B0, int* I0, float* B1, int* I1, int cap1)
 {
     auto in0 = [&](int rv) { return (unsigned)rv - (unsigned)ml <= wm; };
     auto in1 = [&](int rv) {
@@ -862,20 +872,12 @@ __device__ __forceinline__ void gather_runs(const Grp<GS>& q, const K& y, int n,
         if (NR2 >= 2) h = h | ((unsigned)rv - (unsigned)l2 <= w2);
         return h;
     };
-    auto put = [&](float v, int rv, int i) {
-        if (in0(rv)) {
-            const int pos = atomicAdd(&fill[0], 1);
-            if (pos < CAP) {
-                B0[pos] = v;
-                I0[pos] = i;
-            }
-        }
-        if (NR2 > 0 && in1(rv)) {
-            const int pos = atomicAdd(&fill[1], 1);
-            if (pos < CAP1) {
-                B1[pos] = v;
-                I1[pos] = i;
-            }
+    // one gathered key: set 0 (the median run) or 1 (the second runs)
+    auto put = [&](int set, float v, int i) {
+        const int pos = atomicAdd(&fill[set], 1);
+        if (pos < (set ? cap1 : CAP)) {
+            (set ? B1 : B0)[pos] = v;
+            (set ? I1 : I0)[pos] = i;
         }
     };
     const int n4 = n & ~3;
@@ -883,17 +885,23 @@ __device__ __forceinline__ void gather_runs(const Grp<GS>& q, const K& y, int n,
         const float4 y4 = y.get4(i);
         const int r0 = bucket_raw(y4.x, sc, of), r1 = bucket_raw(y4.y, sc, of), r2 = bucket_raw(y4.z, sc, of),
                   r3 = bucket_raw(y4.w, sc, of);
-        const bool hit = (in0(r0) | in0(r1) | in0(r2) | in0(r3)) | (in1(r0) | in1(r1) | in1(r2) | in1(r3));
-        if (hit) {
-            put(y4.x, r0, i);
-            put(y4.y, r1, i + 1);
-            put(y4.z, r2, i + 2);
-            put(y4.w, r3, i + 3);
+        // bit k: key k in the median run; bit 4 + k: key k in a second run
+        unsigned mk = (unsigned)in0(r0) | ((unsigned)in0(r1) << 1) | ((unsigned)in0(r2) << 2) |
+                      ((unsigned)in0(r3) << 3) | ((unsigned)in1(r0) << 4) | ((unsigned)in1(r1) << 5) |
+                      ((unsigned)in1(r2) << 6) | ((unsigned)in1(r3) << 7);
+        while (mk) {   // one pass per gathered key of this thread (most threads: none)
+            const int b = __ffs(mk) - 1;
+            mk &= mk - 1;
+            const int k = b & 3;
+            const float v = k == 0 ? y4.x : (k == 1 ? y4.y : (k == 2 ? y4.z : y4.w));
+            put(b >> 2, v, i + k);
         }
     }
     for (int i = n4 + q.t; i < n; i += GS) {
         const float v = y.get(i);
-        put(v, bucket_raw(v, sc, of), i);
+        const int rv = bucket_raw(v, sc, of);
+        if (in0(rv)) put(0, v, i);
+        if (NR2 > 0 && in1(rv)) put(1, v, i);
     }
 }
 
@@ -941,9 +949,16 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
         if (cnt1 > CAP1) fb = 1;
         r2 = make_int4(b3, b4, OFF, -OFF);   // the run [b3, b4]
     } else if (!ap && !fb) {
-        mad_runs(q, H, C, ba, bb, k2, CAP1, r2, cnt1, c_in);
+        mad_runs(q, H, C, ba, bb, k2, CAP1H, r2, cnt1, c_in);
     }
     const bool second = r2.x <= r2.y;
+    // D_P runs of more than CAP1 keys go to the histogram area past the NB2 counters of the MAD pick: H is
+    // idle from mad_runs until mad_from_runs, which uses only those counters (the |y - med| pass, which
+    // clears all of H, needs the runs no more)
+    const bool runs_in_h = !ap && second && cnt1 > CAP1;
+    float* R1 = runs_in_h ? reinterpret_cast<float*>(H + NB2) : B1;
+    int* J1 = runs_in_h ? reinterpret_cast<int*>(H + NB2 + CAP1H) : I1;
+    const int cap1 = runs_in_h ? CAP1H : CAP1;
     float m1 = qnan, m2 = qnan, p1 = 0.f, p2 = 0.f;
     int im1 = -1, im2 = -1, ip1 = -1, ip2 = -1;
     int npos = 0;
@@ -959,11 +974,11 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
         const unsigned w2 = two_runs ? (unsigned)raw_hi(r2.w) - (unsigned)l2 : 0u;
         int* fill = &C.fill[g][0];
         if (two_runs)
-            gather_runs<GS, 2>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
+            gather_runs<GS, 2>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, R1, J1, cap1);
         else if (second)
-            gather_runs<GS, 1>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
+            gather_runs<GS, 1>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, R1, J1, cap1);
         else
-            gather_runs<GS, 0>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, B1, I1);
+            gather_runs<GS, 0>(q, y, n, sc, of, ml, wm, l1, w1, l2, w2, fill, B0, I0, R1, J1, cap1);
         q.sync();
         gpick(q, B0, I0, cnt0, k1 - c_lo0, k2 - c_lo0, C, m1, m2, im1, im2);
         if (ap) {
@@ -981,7 +996,7 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
             }
         } else {
             const float m = __fmul_rn(__fadd_rn(m1, m2), 0.5f);
-            if (!(second && mad_from_runs<GS, CAP>(q, B1, I1, cnt1, k1 - c_in, k2 - c_in, m, H, B0, I0, C, p1,
+            if (!(second && mad_from_runs<GS, CAP>(q, R1, J1, cnt1, k1 - c_in, k2 - c_in, m, H, B0, I0, C, p1,
                                                        p2, ip1, ip2))) {
                 // |y - med| histogram over [0, 4 sigma_u] (edge bucket clamps), gather, ranks
                 float dmax = D.cov ? 4.0f * C.scale[g] : 0.0f;
@@ -1077,7 +1092,7 @@ __device__ __forceinline__ void select_dir(const Grp<GS>& q, const K& y, Ctl& C,
 // on keys recomputed from X.
 template <int G, int DP4, bool STREAM>
 __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const float* uS, unsigned* hist, float* buf,
-                                            int* ibuf, int n, int npad, bool ap, const DsDev& D, int GA,
+                                            int* ibuf, int n, int npad, int kst, bool ap, const DsDev& D, int GA,
                                             int64_t roff, ResDev* __restrict__ res, int* err, const float* kin)
 {
     constexpr int GS = cta_threads<G>() / G;   // threads per direction group
@@ -1096,7 +1111,7 @@ __device__ __forceinline__ void select_dirs(Ctl& C, const float* keys, const flo
         const KeysRecomputed<DP4> y{D.X32, u, D.ldx, DP4 ? DP4 : ((D.d + 3) & ~3)};
         select_dir<GS>(q, y, C, H, B0, I0, n, ap, D, roff, res, err);
     } else {
-        const KeysArray y{keys + (size_t)g * npad};
+        const KeysArray y{keys + (size_t)g * kst};
         select_dir<GS>(q, y, C, H, B0, I0, n, ap, D, roff, res, err);
     }
 }
@@ -1111,7 +1126,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                                                  const DsDev* __restrict__ dsets, const float* __restrict__ U,
                                                  ResDev* __restrict__ res, int* err, const float* __restrict__ kin)
 {
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) float sm[];
     __shared__ Ctl C;
     const TaskDev T = tasks[blockIdx.x];
     const SlotDev& S = slots[T.slot];
@@ -1119,9 +1134,12 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     const int n = (int)D.n, ldx = D.ldx, d = D.d, dp4 = DP4 ? DP4 : ((d + 3) & ~3);
     const bool ap = (S.kind == 2);
     const int tid = threadIdx.x;
-    const int npad = (n + 3) & ~3;
-    float* keys = sm;                                          // G x npad (none when STREAM)
-    float* uS = keys + (STREAM ? (size_t)0 : (size_t)G * npad);   // G x ldx
+    const int npad = (n + 3) & ~3;   // key stride of the keys formed by launch_pdap_keys (kin)
+    // key stride in shared memory: a multiple of 32 floats, so every direction's keys start on a 128-byte
+    // line and a warp's 32 consecutive keys take one shared-memory wavefront
+    const int kst = pdap_key_stride(n);
+    float* keys = sm;                                          // G x kst (none when STREAM)
+    float* uS = keys + (STREAM ? (size_t)0 : (size_t)G * kst);   // G x ldx
     unsigned* hist = reinterpret_cast<unsigned*>(uS + (size_t)G * ldx);   // G x NB
     float* buf = reinterpret_cast<float*>(hist + (size_t)G * NB);        // G x (CAP + CAP1)
     int* ibuf = reinterpret_cast<int*>(buf + (size_t)G * (CAP + CAP1));  // G x (CAP + CAP1)
@@ -1200,7 +1218,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
         auto emit = [&](int i, const float (&acc)[G]) {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                if (!STREAM) keys[(size_t)g * npad + i] = acc[g];
+                if (!STREAM) keys[(size_t)g * kst + i] = acc[g];
                 atomicAdd(&hist[g * NB + bucket_m(acc[g], sc[g], of[g])], 1u);
             }
         };
@@ -1215,7 +1233,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     if (i + h < n) {
-                        if (!STREAM) keys[(size_t)g * npad + i + h] = kv[h];
+                        if (!STREAM) keys[(size_t)g * kst + i + h] = kv[h];
                         atomicAdd(&hist[g * NB + bucket_m(kv[h], sc[g], of[g])], 1u);
                     }
                 }
@@ -1236,9 +1254,9 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
                 float xv[D4];
                 load_row<D4>(D, i, ldx, xv);
                 const float ka = key_halves<D4>(ua, xv), kb = key_halves<D4>(ub, xv);
-                if (!STREAM) keys[(size_t)(2 * pair) * npad + i] = ka;
+                if (!STREAM) keys[(size_t)(2 * pair) * kst + i] = ka;
                 atomicAdd(&hist[(2 * pair) * NB + bucket_m(ka, sca, ofa)], 1u);
-                if (!STREAM) keys[(size_t)(2 * pair + 1) * npad + i] = kb;
+                if (!STREAM) keys[(size_t)(2 * pair + 1) * kst + i] = kb;
                 atomicAdd(&hist[(2 * pair + 1) * NB + bucket_m(kb, scb, ofb)], 1u);
             }
         } else if (DP4 > 0) {
@@ -1259,10 +1277,10 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
             if (D.Xt)
                 pass_a_rows<G, D4, STREAM, 32, NTK>(reinterpret_cast<const float4*>(D.Xt) +
                                                         ((size_t)(tid >> 5) * c4 * 32 + (tid & 31)),
-                                                    rstep, tid, n, npad, uu, sc, of, keys, hist);
+                                                    rstep, tid, n, kst, uu, sc, of, keys, hist);
             else
                 pass_a_rows<G, D4, STREAM, 1, NTK>(reinterpret_cast<const float4*>(D.X32) + (size_t)tid * c4, rstep,
-                                                   tid, n, npad, uu, sc, of, keys, hist);
+                                                   tid, n, kst, uu, sc, of, keys, hist);
         } else {
             for (int i = tid; i < n; i += NTK) {
                 const float4* xr = reinterpret_cast<const float4*>(D.X32 + (int64_t)i * ldx);
@@ -1286,7 +1304,7 @@ __global__ void __launch_bounds__(cta_threads<G>(), (G >= 4 ? 1 : 2)) k_pdap2(co
     }
     __syncthreads();
 
-    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, ibuf, n, npad, ap, D, GA, S.roff + T.j0, res, err, kin);
+    select_dirs<G, DP4, STREAM>(C, keys, uS, hist, buf, ibuf, n, npad, kst, ap, D, GA, S.roff + T.j0, res, err, kin);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1859,8 +1877,8 @@ __global__ void __launch_bounds__(WNT, 2) k_pdapw(const TaskDev* __restrict__ ta
 
 size_t pdap_smem_bytes(int n, int group, int ldx, bool stream)
 {
-    const size_t npad = stream ? 0 : ((size_t)n + 3) & ~(size_t)3;
-    return sizeof(float) * ((size_t)group * npad + (size_t)group * ldx) + sizeof(unsigned) * (size_t)group * NB +
+    const size_t kst = stream ? 0 : (size_t)pdap_key_stride(n);
+    return sizeof(float) * ((size_t)group * kst + (size_t)group * ldx) + sizeof(unsigned) * (size_t)group * NB +
            (sizeof(float) + sizeof(int)) * (size_t)group * (CAP + CAP1);
 }
 
