@@ -59,7 +59,7 @@ CAPTURED = {
     # k_pdap2<2,12>, d = 10, n = 10,000, 50,000 directions per launch: rounds 10-12 of each kind (six launches
     # of the first warm-up step): DRAM bytes and warp instructions per (point, direction) element, averaged
     "k_pdap2_c2": {"src": ("paper_2506_08262_gb300/csrc/pdap.cu", "paper_2506_08262_gb300/csrc/rrs_internal.h"),
-                   "src_sha16": "b1095d24331c8f9a", "traffic": 3.534e6, "warp_instr_per_element": 2.535},
+                   "src_sha16": "8f7dbf26a8a98cf6", "traffic": 3.548e6, "warp_instr_per_element": 2.105},
     # k_hd_tc<256>, 10,000 queries x 100 directions x 100,000 points, d = 50: one launch
     "k_hd_tc_c3": {"src": ("paper_2506_08262_gb300/csrc/hd_tc.cu", "paper_2506_08262_gb300/csrc/async_sync.cuh",
                            "paper_2506_08262_gb300/csrc/rrs_device.cuh"),
